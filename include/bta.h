@@ -1,0 +1,185 @@
+/*
+ * bta.h -- C ABI of the GB300 (sm_103a) BTA block-Cholesky / selected-inversion library.
+ *
+ * A BTA matrix (paper, Section 2.1, Table 2) is symmetric positive definite, with
+ * n diagonal blocks of size b, the sub/super-diagonal blocks, and an arrowhead of
+ * a rows and columns whose a x a corner is the "arrow tip"; N = n*b + a. a = 0 is
+ * the plain block-tridiagonal case.
+ *
+ * Storage (all entry points): FP64, row-major, C-contiguous DEVICE memory owned
+ * by the caller. Only the lower block pattern is stored:
+ *   diag  [n][b][b]     A_{i,i}
+ *   lower [n-1][b][b]   A_{i+1,i}        (may be NULL when n == 1)
+ *   arrow [n][a][b]     A_{n,i}          (may be NULL when a == 0)
+ *   tip   [a][a]        A_{n,n}          (may be NULL when a == 0)
+ *   rhs   [N][nrhs]     right-hand sides, row-major
+ * Every pointer must be 8-byte aligned. All calls are asynchronous on `stream`
+ * (a cudaStream_t; NULL means the legacy default stream) and only enqueue work.
+ *
+ * Return codes (synchronous, about the arguments and the launch only):
+ *   0                   enqueued
+ *   -k (k = 1, 2, ...)  argument k is invalid (out of range, NULL where a
+ *                       buffer is needed, misaligned, or workspace too small)
+ *   > 0                 a CUDA error code raised while enqueueing
+ * Numerical failure is asynchronous: a non-positive pivot in bta_factor sets the
+ * library's per-device info word (read it with bta_get_info) and the outputs from
+ * the failing block column on become NaN. Nothing traps.
+ *
+ * Ordering: bta_factor -> { bta_logdet, bta_solve } -> bta_selinv. bta_selinv
+ * overwrites the factor with the selected inverse (like LAPACK POTRI), so call
+ * logdet and solve before it, or on a copy.
+ *
+ * Scratch memory: the plain entry points allocate their scratch stream-ordered
+ * (cudaMallocAsync / cudaFreeAsync on `stream`). The *_ws variants take a
+ * caller-owned device workspace of at least bta_workspace_bytes(...) bytes
+ * (256-byte aligned) and allocate nothing; a workspace must not be shared by
+ * calls that can run concurrently.
+ */
+#ifndef BTA_H_
+#define BTA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* bta_stream_t; /* same type as cudaStream_t */
+
+/* Operation selectors for bta_workspace_bytes. */
+#define BTA_OP_FACTOR 1
+#define BTA_OP_SELINV 2
+#define BTA_OP_SOLVE 3
+#define BTA_OP_LOGDET 4
+
+/*
+ * bta_factor -- block Cholesky A = L L^T in place (paper, Algorithm 1, POBTAF;
+ * Section 2.2). For i = 0..n-2: L_ii = POTRF(A_ii); L_{i+1,i} = A_{i+1,i} L_ii^{-T};
+ * L_{n,i} = A_{n,i} L_ii^{-T}; A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T;
+ * A_{n,i+1} -= L_{n,i} L_{i+1,i}^T; A_{n,n} -= L_{n,i} L_{n,i}^T; then the last
+ * block column and L_nn = POTRF(A_nn).
+ * In: the lower triangles of diag[i] and tip (upper triangles are not read),
+ * lower, arrow. Out: L in the same buffers; the strict upper triangles of diag[i]
+ * and tip are set to zero. The triangular solves run as L_ii^{-1} followed by
+ * products (the inverse-plus-GEMM substitution of Sections 4 and 5.1).
+ * Errors: see the header comment; info = 1-based global row of the first
+ * non-positive leading minor (block i, local row j -> i*b + j; tip -> n*b + j).
+ */
+int bta_factor(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+               double* arrow, double* tip, bta_stream_t stream);
+
+/*
+ * bta_selinv -- selected inversion (paper, Algorithm 2, POBTASI; Section 2.2):
+ * overwrites the factor L (as left by bta_factor) with X = A^{-1} restricted to
+ * the BTA pattern: X_{i,i} (returned full and symmetric), X_{i+1,i}, X_{n,i} and
+ * X_{n,n}. X_nn = L_nn^{-T} L_nn^{-1}; for i = n-1..0:
+ *   X_{i+1,i} = -(X_{i+1,i+1} L_{i+1,i} + X_{n,i+1}^T L_{n,i}) L_ii^{-1}
+ *   X_{n,i}   = -(X_{n,i+1}  L_{i+1,i} + X_{n,n}     L_{n,i}) L_ii^{-1}
+ *   X_{i,i}   = (L_ii^{-T} - X_{i+1,i}^T L_{i+1,i} - X_{n,i}^T L_{n,i}) L_ii^{-1}
+ * evaluated with G_i = L_{i+1,i} L_ii^{-1}, H_i = L_{n,i} L_ii^{-1} and
+ * M_i = L_ii^{-T} L_ii^{-1} formed for all i before the backward sweep.
+ */
+int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+               double* arrow, double* tip, bta_stream_t stream);
+
+/*
+ * bta_solve -- solves A x = rhs in place given the factor L (block forward
+ * substitution L y = rhs, then backward L^T x = y). Not in the paper; it is the
+ * standard use of a Cholesky factor.
+ *   y_i = L_ii^{-1}(r_i - L_{i,i-1} y_{i-1}),  y_n = L_nn^{-1}(r_n - sum_i L_{n,i} y_i)
+ *   x_n = L_nn^{-T} y_n,  x_i = L_ii^{-T}(y_i - L_{i+1,i}^T x_{i+1} - L_{n,i}^T x_n)
+ * rhs: [N][nrhs] row-major device buffer, 1 <= nrhs <= 64.
+ */
+int bta_solve(int64_t n, int64_t b, int64_t a, const double* diag,
+              const double* lower, const double* arrow, const double* tip,
+              double* rhs, int64_t nrhs, bta_stream_t stream);
+
+/*
+ * bta_logdet -- log det A = 2 * (sum_i sum_k log (L_ii)_kk + sum_k log (L_nn)_kk)
+ * from the factor (not in the paper: det A = det(L)^2). Summed in FP64 in a fixed
+ * order (per-block tree sums, then blocks in order, then the tip), so repeated
+ * calls give identical bits. out_dev: one double in device memory.
+ */
+int bta_logdet(int64_t n, int64_t b, int64_t a, const double* diag,
+               const double* tip, double* out_dev, bta_stream_t stream);
+
+/*
+ * bta_get_info -- synchronizes `stream`, returns the current device's info word
+ * in *info (0: every pivot positive since the last read; k > 0: LAPACK-style
+ * global row of the first failed pivot) and resets it to 0. The word is shared by
+ * all calls on the device: failures of concurrent calls on different streams are
+ * not told apart.
+ */
+int bta_get_info(bta_stream_t stream, int64_t* info);
+
+/*
+ * bta_workspace_bytes -- scratch bytes the *_ws variant of operation `op`
+ * (BTA_OP_*) needs for these sizes; nrhs is used by BTA_OP_SOLVE only.
+ * Returns 0 for invalid arguments or an operation that needs no scratch.
+ */
+size_t bta_workspace_bytes(int op, int64_t n, int64_t b, int64_t a, int64_t nrhs);
+
+/* The same operations on a caller-owned workspace (see bta_workspace_bytes);
+ * they allocate nothing. */
+int bta_factor_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                  double* arrow, double* tip, void* ws, size_t ws_bytes,
+                  bta_stream_t stream);
+int bta_selinv_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                  double* arrow, double* tip, void* ws, size_t ws_bytes,
+                  bta_stream_t stream);
+int bta_solve_ws(int64_t n, int64_t b, int64_t a, const double* diag,
+                 const double* lower, const double* arrow, const double* tip,
+                 double* rhs, int64_t nrhs, void* ws, size_t ws_bytes,
+                 bta_stream_t stream);
+int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag,
+                  const double* tip, double* out_dev, void* ws, size_t ws_bytes,
+                  bta_stream_t stream);
+
+/* ---- Measurement support (not part of the method) ----------------------- */
+
+/* Kernel ids for bta_timing_read. */
+#define BTA_KERNEL_GEMM 0       /* DMMA tile GEMM (Schur updates, TRMM, selinv chain) */
+#define BTA_KERNEL_POTRF_TILE 1 /* diagonal-tile Cholesky */
+#define BTA_KERNEL_TRSM_PANEL 2 /* panel triangular solve inside POTRF */
+#define BTA_KERNEL_TILE_INV 3   /* diagonal-tile inverse inside TRTRI */
+#define BTA_KERNEL_ZERO_UPPER 4
+#define BTA_KERNEL_MIRROR 5
+#define BTA_KERNEL_LOGDET 6
+#define BTA_KERNEL_TRSV 7
+#define BTA_KERNEL_GEMV 8
+#define BTA_KERNEL_ARROW 9
+#define BTA_KERNEL_PROBE 10
+
+/*
+ * bta_timing_enable -- on != 0: from now on every kernel launch of the library
+ * is bracketed by CUDA events on its stream and tagged with its algorithmic
+ * FP64 flop count; previous records are dropped. on == 0 stops recording. Off by
+ * default. Host-side cost per launch; meant for measurement runs only.
+ */
+int bta_timing_enable(int on);
+
+/*
+ * bta_timing_read -- waits for the recorded launches of kernel `kernel_id`
+ * (BTA_KERNEL_*) and returns their summed device time (ms), summed algorithmic
+ * flops and launch count.
+ */
+int bta_timing_read(int kernel_id, double* total_ms, double* flops, int64_t* launches);
+
+/*
+ * bta_probe_fp64_peak -- enqueues a DMMA (mma.sync m8n8k4 f64) throughput
+ * kernel on every SM of the current device; *flops receives its flop count
+ * (host, at enqueue). Time it with events on `stream` to measure the FP64
+ * tensor peak that bounds this library's kernels. out_dev: one device double
+ * (written only in a case that cannot occur; keeps the loop live).
+ */
+int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops, bta_stream_t stream);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bta_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTA_H_ */

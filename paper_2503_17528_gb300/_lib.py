@@ -1,0 +1,57 @@
+"""ctypes loader for libbta.so (the C ABI declared in include/bta.h).
+
+Loading fails loudly: there is no fallback path. Build the library with
+``python -m paper_2503_17528_gb300.build`` (or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbta.so")
+
+_i64 = ctypes.c_int64
+_p = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+# name -> argtypes (every entry point returns int, except bta_workspace_bytes)
+_SIGS = {
+    "bta_factor": [_i64, _i64, _i64, _p, _p, _p, _p, _p],
+    "bta_selinv": [_i64, _i64, _i64, _p, _p, _p, _p, _p],
+    "bta_solve": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p],
+    "bta_logdet": [_i64, _i64, _i64, _p, _p, _p, _p],
+    "bta_get_info": [_p, ctypes.POINTER(_i64)],
+    "bta_workspace_bytes": [ctypes.c_int, _i64, _i64, _i64, _i64],
+    "bta_factor_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _sz, _p],
+    "bta_selinv_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _sz, _p],
+    "bta_solve_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _sz, _p],
+    "bta_logdet_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _sz, _p],
+    "bta_timing_enable": [ctypes.c_int],
+    "bta_timing_read": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(_i64)],
+    "bta_probe_fp64_peak": [_p, _i64, ctypes.POINTER(ctypes.c_double), _p],
+    "bta_version": [],
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libbta.so once; raises if it is missing or lacks a symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it first (paper_2503_17528_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = _sz if name == "bta_workspace_bytes" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)

@@ -1,0 +1,131 @@
+"""Torch-facing binding of the C ABI (argument marshalling only).
+
+Each function takes FP64 CUDA tensors in block storage, checks shapes and
+device placement, and calls the same-named C entry point on the current torch
+stream with a workspace tensor from torch's allocator. No computation happens
+here.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+OP_FACTOR, OP_SELINV, OP_SOLVE, OP_LOGDET = 1, 2, 3, 4
+
+
+class BTAError(RuntimeError):
+    pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check(rc: int, name: str):
+    if rc != 0:
+        if rc < 0:
+            raise BTAError(f"{name}: invalid argument {-rc} (return code {rc})")
+        raise BTAError(f"{name}: CUDA error {rc}")
+
+
+def _dims(diag, lower, arrow, tip):
+    if diag.dim() != 3 or diag.shape[1] != diag.shape[2]:
+        raise ValueError("diag must be [n, b, b]")
+    n, b = diag.shape[0], diag.shape[1]
+    a = tip.shape[0] if tip is not None else 0
+    for name, t, shape in (("lower", lower, (n - 1, b, b)), ("arrow", arrow, (n, a, b)),
+                           ("tip", tip, (a, a))):
+        if t is None:
+            if (name == "lower" and n > 1) or (name != "lower" and a > 0):
+                raise ValueError(f"{name} is required")
+            continue
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    for t in (diag, lower, arrow, tip):
+        if t is None:
+            continue
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("blocks must be contiguous float64 CUDA tensors")
+        if t.device != diag.device:
+            raise ValueError("all blocks must be on one device")
+    return n, b, a
+
+
+def workspace_bytes(op: int, n: int, b: int, a: int, nrhs: int = 1) -> int:
+    return int(_lib.load().bta_workspace_bytes(op, n, b, a, nrhs))
+
+
+def _workspace(op, n, b, a, device, nrhs=1):
+    nbytes = workspace_bytes(op, n, b, a, nrhs)
+    ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws, ctypes.c_void_p(ws.data_ptr() + off), nbytes
+
+
+def factor(diag, lower, arrow, tip):
+    """In place: A -> L (Algorithm 1). Returns the same tensors."""
+    n, b, a = _dims(diag, lower, arrow, tip)
+    lib = _lib.load()
+    with torch.cuda.device(diag.device):
+        ws, wp, nb = _workspace(OP_FACTOR, n, b, a, diag.device)
+        _check(lib.bta_factor_ws(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                 wp, nb, _stream(diag.device)), "bta_factor")
+    return diag, lower, arrow, tip
+
+
+def selinv(diag, lower, arrow, tip):
+    """In place: L -> X, the selected inverse on the BTA pattern (Algorithm 2)."""
+    n, b, a = _dims(diag, lower, arrow, tip)
+    lib = _lib.load()
+    with torch.cuda.device(diag.device):
+        ws, wp, nb = _workspace(OP_SELINV, n, b, a, diag.device)
+        _check(lib.bta_selinv_ws(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                 wp, nb, _stream(diag.device)), "bta_selinv")
+    return diag, lower, arrow, tip
+
+
+def solve(diag, lower, arrow, tip, rhs):
+    """In place on rhs [N, nrhs] (or [N]): rhs <- A^{-1} rhs, given the factor L."""
+    n, b, a = _dims(diag, lower, arrow, tip)
+    if rhs.dtype != torch.float64 or not rhs.is_cuda or not rhs.is_contiguous():
+        raise ValueError("rhs must be a contiguous float64 CUDA tensor")
+    nrhs = 1 if rhs.dim() == 1 else rhs.shape[1]
+    if rhs.shape[0] != n * b + a:
+        raise ValueError("rhs must have n*b + a rows")
+    lib = _lib.load()
+    with torch.cuda.device(diag.device):
+        ws, wp, nb = _workspace(OP_SOLVE, n, b, a, diag.device, nrhs)
+        _check(lib.bta_solve_ws(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                _ptr(rhs), nrhs, wp, nb, _stream(diag.device)), "bta_solve")
+    return rhs
+
+
+def logdet(diag, tip, out=None):
+    """log det A from the factor; returns a 0-d float64 CUDA tensor (no host sync)."""
+    n, b = diag.shape[0], diag.shape[1]
+    a = tip.shape[0] if tip is not None else 0
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=diag.device)
+    lib = _lib.load()
+    with torch.cuda.device(diag.device):
+        ws, wp, nb = _workspace(OP_LOGDET, n, b, a, diag.device)
+        _check(lib.bta_logdet_ws(n, b, a, _ptr(diag), _ptr(tip), _ptr(out), wp, nb,
+                                 _stream(diag.device)), "bta_logdet")
+    return out
+
+
+def get_info(device=None) -> int:
+    """Synchronizes the current stream and returns (and clears) the info word."""
+    lib = _lib.load()
+    v = ctypes.c_int64(0)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with torch.cuda.device(dev):
+        _check(lib.bta_get_info(_stream(dev), ctypes.byref(v)), "bta_get_info")
+    return int(v.value)

@@ -1,0 +1,398 @@
+// C ABI of the BTA library (declared in include/bta.h): argument checks,
+// workspace layout and the launch sequences of factor, selinv, solve, logdet.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bta.h"
+#include "bta_internal.cuh"
+
+using namespace bta;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline bool misaligned(const void* p) { return ((uintptr_t)p & 7u) != 0; }
+
+#define BTA_TRY(expr)                                   \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return (int)e_;              \
+  } while (0)
+
+// Workspace carving: consecutive 256-byte aligned regions.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* p) : base((char*)p) {}
+  double* take(size_t count) {
+    double* p = base ? (double*)(base + off) : nullptr;
+    off += align_up(count * sizeof(double));
+    return p;
+  }
+};
+
+struct FactorWs { double *Linv, *W, *Wa; };
+struct SelinvWs { double *Linv, *G, *H, *LtInv; };
+struct SolveWs { double* partial; };
+struct LogdetWs { double* partial; };
+
+size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o) {
+  (void)n;
+  Carver c(p);
+  FactorWs w;
+  w.Linv = c.take((size_t)(b * b));
+  w.W = c.take((size_t)(b * b));
+  w.Wa = c.take((size_t)(a * b + 1));
+  if (o) *o = w;
+  return c.off;
+}
+
+size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o) {
+  Carver c(p);
+  SelinvWs w;
+  w.Linv = c.take((size_t)(n * b * b));
+  w.G = c.take((size_t)((n - 1) * b * b + 1));
+  w.H = c.take((size_t)(n * a * b + 1));
+  w.LtInv = c.take((size_t)(a * a + 1));
+  if (o) *o = w;
+  return c.off;
+}
+
+size_t solve_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, SolveWs* o) {
+  (void)b;
+  Carver c(p);
+  SolveWs w;
+  w.partial = c.take((size_t)(arrow_chunks(n) * a * R + 1));
+  if (o) *o = w;
+  return c.off;
+}
+
+size_t logdet_ws(int64_t n, void* p, LogdetWs* o) {
+  Carver c(p);
+  LogdetWs w;
+  w.partial = c.take((size_t)(n + 1));
+  if (o) *o = w;
+  return c.off;
+}
+
+// Shared checks; argument positions follow the C signatures (1-based).
+int check_sizes(int64_t n, int64_t b, int64_t a) {
+  if (n < 1 || n > (1 << 24)) return -1;
+  if (b < 1 || b > 32768) return -2;
+  if (a < 0 || a > 32768) return -3;
+  return 0;
+}
+
+int check_blocks(int64_t n, int64_t a, const double* diag, const double* lower,
+                 const double* arrow, const double* tip) {
+  if (!diag || misaligned(diag)) return -4;
+  if (n > 1 && (!lower || misaligned(lower))) return -5;
+  if (a > 0 && (!arrow || misaligned(arrow))) return -6;
+  if (a > 0 && (!tip || misaligned(tip))) return -7;
+  return 0;
+}
+
+GemmArgs one_term(const GemmTerm& t, double* C, int64_t ldc, int M, int N, double beta,
+                  int lowerC) {
+  GemmArgs g{};
+  g.t[0] = t;
+  g.nterms = 1;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.beta = beta;
+  g.lowerC = lowerC;
+  g.nb1 = 1;
+  g.nb2 = 1;
+  return g;
+}
+
+int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                double* tip, const FactorWs& w, cudaStream_t s) {
+  const int B = (int)b, Aa = (int)a;
+  const int64_t bb = b * b;
+  for (int64_t i = 0; i < n; ++i) {
+    double* Di = diag + i * bb;
+    BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+    BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s));
+    if (i + 1 < n) {
+      double* Li = lower + i * bb;
+      // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
+      BTA_TRY(gemm_f64(one_term(term(Li, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
+                                w.W, b, B, B, 0.0, 0), s));
+      BTA_TRY(cudaMemcpyAsync(Li, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
+      BTA_TRY(gemm_f64(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
+                                Di + bb, b, B, B, 1.0, 1), s));
+    }
+    if (a > 0) {
+      double* Ai = arrow + i * a * b;
+      // L_{n,i} = A_{n,i} L_ii^{-T}
+      BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
+                                w.Wa, b, Aa, B, 0.0, 0), s));
+      BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (i + 1 < n) {
+        // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
+        BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, lower + i * bb, b, OP_T, TRI_NONE,
+                                       B, -1.0),
+                                  Ai + a * b, b, Aa, B, 1.0, 0), s));
+      }
+      // A_{n,n} -= L_{n,i} L_{n,i}^T
+      BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
+                                tip, a, Aa, Aa, 1.0, 1), s));
+    }
+  }
+  if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
+  return 0;
+}
+
+int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                double* tip, const SelinvWs& w, cudaStream_t s) {
+  const int B = (int)b, Aa = (int)a;
+  const int64_t bb = b * b, ab = a * b;
+  // Prologue, independent over i: L_ii^{-1}, G_i, H_i, M_i; then X_nn.
+  BTA_TRY(trtri_blocks(diag, b, bb, w.Linv, b, bb, (int)n, B, s));
+  if (n > 1) {
+    GemmArgs g = one_term(term(lower, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
+                          w.G, b, B, B, 0.0, 0);
+    g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)(n - 1);
+    BTA_TRY(gemm_f64(g, s));
+  }
+  if (a > 0) {
+    GemmArgs g = one_term(term(arrow, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
+                          w.H, b, Aa, B, 0.0, 0);
+    g.t[0].sA1 = ab; g.t[0].sB1 = bb; g.sC1 = ab; g.nb1 = (int)n;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  {
+    GemmArgs g = one_term(term(w.Linv, b, OP_T, TRI_UPPER, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
+                          diag, b, B, B, 0.0, 1);
+    g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)n;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  if (a > 0) {
+    BTA_TRY(trtri_blocks(tip, a, a * a, w.LtInv, a, a * a, 1, Aa, s));
+    BTA_TRY(gemm_f64(one_term(term(w.LtInv, a, OP_T, TRI_UPPER, w.LtInv, a, OP_N, TRI_LOWER, Aa,
+                                   1.0),
+                              tip, a, Aa, Aa, 0.0, 0), s));
+  }
+  // Backward sweep.
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double* Di = diag + i * bb;
+    const double* Gi = w.G + i * bb;
+    const double* Hi = w.H + i * ab;
+    if (i + 1 < n) {
+      // X_{i+1,i} = -X_{i+1,i+1} G_i - X_{n,i+1}^T H_i
+      GemmArgs g = one_term(term(Di + bb, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0),
+                            lower + i * bb, b, B, B, 0.0, 0);
+      if (a > 0) {
+        g.t[1] = term(arrow + (i + 1) * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
+        g.nterms = 2;
+      }
+      BTA_TRY(gemm_f64(g, s));
+    }
+    if (a > 0) {
+      // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i
+      GemmArgs g = one_term(term(tip, a, OP_N, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0),
+                            arrow + i * ab, b, Aa, B, 0.0, 0);
+      if (i + 1 < n) {
+        g.t[1] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
+        g.nterms = 2;
+      }
+      BTA_TRY(gemm_f64(g, s));
+    }
+    // X_ii = M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i  (lower tiles, then mirrored)
+    GemmArgs g{};
+    g.C = Di; g.ldc = b; g.M = B; g.N = B; g.beta = 1.0; g.lowerC = 1; g.nb1 = 1; g.nb2 = 1;
+    if (i + 1 < n)
+      g.t[g.nterms++] = term(lower + i * bb, b, OP_T, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
+    if (a > 0)
+      g.t[g.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
+    if (g.nterms) BTA_TRY(gemm_f64(g, s));
+    BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
+  }
+  return 0;
+}
+
+int solve_impl(int64_t n, int64_t b, int64_t a, const double* diag, const double* lower,
+               const double* arrow, const double* tip, double* rhs, int64_t R,
+               const SolveWs& w, cudaStream_t s) {
+  const int B = (int)b, Rr = (int)R;
+  const int64_t bb = b * b, bR = b * R;
+  double* rn = rhs + n * bR;
+  for (int64_t i = 0; i < n; ++i) {
+    if (i > 0)
+      BTA_TRY(gemv_multi(lower + (i - 1) * bb, b, OP_N, B, B, rhs + (i - 1) * bR, R,
+                         rhs + i * bR, R, Rr, -1.0, s));
+    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, false, s));
+  }
+  if (a > 0) {
+    BTA_TRY(arrow_gather(arrow, n, b, a, rhs, Rr, w.partial, arrow_chunks(n), rn, s));
+    BTA_TRY(trsv_lower(tip, a, (int)a, rn, R, Rr, false, s));
+    BTA_TRY(trsv_lower(tip, a, (int)a, rn, R, Rr, true, s));
+    BTA_TRY(arrow_scatter(arrow, n, b, a, rn, Rr, rhs, s));
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    if (i + 1 < n)
+      BTA_TRY(gemv_multi(lower + i * bb, b, OP_T, B, B, rhs + (i + 1) * bR, R, rhs + i * bR, R,
+                         Rr, -1.0, s));
+    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, true, s));
+  }
+  return 0;
+}
+
+// Runs `body(ws)` on a stream-ordered temporary workspace of `bytes`.
+template <class F>
+int with_async_ws(size_t bytes, cudaStream_t s, F body) {
+  void* p = nullptr;
+  if (bytes) BTA_TRY(cudaMallocAsync(&p, bytes, s));
+  const int rc = body(p);
+  if (p) {
+    cudaError_t e = cudaFreeAsync(p, s);
+    if (rc == 0 && e != cudaSuccess) return (int)e;
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bta_version(void) { return 100; }
+
+size_t bta_workspace_bytes(int op, int64_t n, int64_t b, int64_t a, int64_t nrhs) {
+  if (check_sizes(n, b, a)) return 0;
+  switch (op) {
+    case BTA_OP_FACTOR: return factor_ws(n, b, a, nullptr, nullptr);
+    case BTA_OP_SELINV: return selinv_ws(n, b, a, nullptr, nullptr);
+    case BTA_OP_SOLVE:
+      if (nrhs < 1 || nrhs > 64) return 0;
+      return solve_ws(n, b, a, nrhs, nullptr, nullptr);
+    case BTA_OP_LOGDET: return logdet_ws(n, nullptr, nullptr);
+    default: return 0;
+  }
+}
+
+int bta_factor_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                  double* tip, void* ws, size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  FactorWs w;
+  const size_t need = factor_ws(n, b, a, ws, &w);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -8;
+  if (ws_bytes < need) return -9;
+  return factor_impl(n, b, a, diag, lower, arrow, tip, w, (cudaStream_t)stream);
+}
+
+int bta_factor(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+               double* tip, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  const size_t need = factor_ws(n, b, a, nullptr, nullptr);
+  return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
+    return bta_factor_ws(n, b, a, diag, lower, arrow, tip, p, need, stream);
+  });
+}
+
+int bta_selinv_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                  double* tip, void* ws, size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  SelinvWs w;
+  const size_t need = selinv_ws(n, b, a, ws, &w);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -8;
+  if (ws_bytes < need) return -9;
+  return selinv_impl(n, b, a, diag, lower, arrow, tip, w, (cudaStream_t)stream);
+}
+
+int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+               double* tip, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  const size_t need = selinv_ws(n, b, a, nullptr, nullptr);
+  return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
+    return bta_selinv_ws(n, b, a, diag, lower, arrow, tip, p, need, stream);
+  });
+}
+
+int bta_solve_ws(int64_t n, int64_t b, int64_t a, const double* diag, const double* lower,
+                 const double* arrow, const double* tip, double* rhs, int64_t nrhs, void* ws,
+                 size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  if (!rhs || misaligned(rhs)) return -8;
+  if (nrhs < 1 || nrhs > 64) return -9;
+  SolveWs w;
+  const size_t need = solve_ws(n, b, a, nrhs, ws, &w);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -10;
+  if (ws_bytes < need) return -11;
+  return solve_impl(n, b, a, diag, lower, arrow, tip, rhs, nrhs, w, (cudaStream_t)stream);
+}
+
+int bta_solve(int64_t n, int64_t b, int64_t a, const double* diag, const double* lower,
+              const double* arrow, const double* tip, double* rhs, int64_t nrhs,
+              bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  if (!rhs || misaligned(rhs)) return -8;
+  if (nrhs < 1 || nrhs > 64) return -9;
+  const size_t need = solve_ws(n, b, a, nrhs, nullptr, nullptr);
+  return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
+    return bta_solve_ws(n, b, a, diag, lower, arrow, tip, rhs, nrhs, p, need, stream);
+  });
+}
+
+int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag, const double* tip,
+                  double* out_dev, void* ws, size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (rc) return rc;
+  if (!diag || misaligned(diag)) return -4;
+  if (a > 0 && (!tip || misaligned(tip))) return -5;
+  if (!out_dev || misaligned(out_dev)) return -6;
+  LogdetWs w;
+  const size_t need = logdet_ws(n, ws, &w);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -7;
+  if (ws_bytes < need) return -8;
+  BTA_TRY(logdet_f64(diag, n, b, tip, a, w.partial, out_dev, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_logdet(int64_t n, int64_t b, int64_t a, const double* diag, const double* tip,
+               double* out_dev, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (rc) return rc;
+  if (!diag || misaligned(diag)) return -4;
+  if (a > 0 && (!tip || misaligned(tip))) return -5;
+  if (!out_dev || misaligned(out_dev)) return -6;
+  const size_t need = logdet_ws(n, nullptr, nullptr);
+  return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
+    return bta_logdet_ws(n, b, a, diag, tip, out_dev, p, need, stream);
+  });
+}
+
+int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,
+                        bta_stream_t stream) {
+  if (!out_dev) return -1;
+  if (iters < 1) return -2;
+  if (!flops) return -3;
+  BTA_TRY(fp64_probe(out_dev, iters, flops, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_get_info(bta_stream_t stream, int64_t* info) {
+  if (!info) return -2;
+  long long v = 0;
+  BTA_TRY(info_read_reset((cudaStream_t)stream, &v));
+  *info = (int64_t)v;
+  return 0;
+}
+
+}  // extern "C"

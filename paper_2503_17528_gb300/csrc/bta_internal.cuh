@@ -1,0 +1,96 @@
+// Internal interfaces between the C-ABI layer (bta_api.cu) and the FP64 kernels
+// (kernels_f64.cu). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bta {
+
+constexpr int T = 32;  // edge of every FP64 tile
+
+enum { OP_N = 0, OP_T = 1 };
+// Structure of op(X) for a GEMM operand; lets a tile skip the k-range that is
+// known to be zero (triangular factors and inverses).
+enum { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+// One product term alpha * op(A) * op(B) with op(A): M x K, op(B): K x N.
+struct GemmTerm {
+  const double* A;
+  const double* B;
+  int64_t lda, ldb;  // row strides (elements) of the stored A and B
+  int64_t sA1, sB1;  // strides per unit of batch index z1
+  int64_t sA2, sB2;  // strides per unit of batch index z2
+  int K;
+  int opA, opB, triA, triB;
+  double alpha;
+};
+
+// C = beta * C + sum_t alpha_t op(A_t) op(B_t) over a 2-D batch (z1, z2).
+struct GemmArgs {
+  GemmTerm t[2];
+  int nterms;
+  double* C;
+  int64_t ldc, sC1, sC2;
+  int M, N;
+  double beta;  // C is read only if beta != 0
+  int lowerC;   // 1: only output tiles with tile_row >= tile_col are computed
+  int nb1, nb2;
+};
+
+inline GemmTerm term(const double* A, int64_t lda, int opA, int triA,
+                     const double* B, int64_t ldb, int opB, int triB, int K,
+                     double alpha) {
+  GemmTerm t{};
+  t.A = A; t.B = B; t.lda = lda; t.ldb = ldb; t.K = K;
+  t.opA = opA; t.opB = opB; t.triA = triA; t.triB = triB; t.alpha = alpha;
+  return t;
+}
+
+cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s);
+
+// Dense block kernels (all FP64, row-major, leading dimension ld; `count`
+// blocks at stride `sb` elements; square blocks of order `nrow`).
+// Lower Cholesky in place; zeroes the strict upper triangle. info_row0 is the
+// 1-based global row of the first row of block 0, info_rstride the increase
+// per block.
+cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
+                         long long info_row0, long long info_rstride,
+                         cudaStream_t s);
+// Inverse of lower-triangular blocks: Linv (separate buffer, same layout) =
+// L^{-1}, strict upper triangle zero.
+cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Linv,
+                         int64_t ldi, int64_t si, int count, int nrow,
+                         cudaStream_t s);
+// Copy the lower triangle onto the upper one (symmetrize) for `count` blocks.
+cudaError_t mirror_lower(double* A, int64_t ld, int64_t sb, int count, int nrow,
+                         cudaStream_t s);
+
+// log det from factor blocks: out = 2 * (sum log diag(L_ii) + sum log diag(L_nn)).
+cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b,
+                       const double* tip, int64_t a, double* partial,
+                       double* out, cudaStream_t s);
+
+// Solve pieces (rhs row-major [rows][R]).
+cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x,
+                       int64_t ldx, int R, bool trans, cudaStream_t s);
+// x[M][R] += alpha * op(A) * y[K][R], op(A) is M x K.
+cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K,
+                       const double* y, int64_t ldy, double* x, int64_t ldx,
+                       int R, double alpha, cudaStream_t s);
+// r_n[a][R] -= sum_i arrow[i] (a x b) * y_i (b x R), y_i = rhs block i.
+cudaError_t arrow_gather(const double* arrow, int64_t n, int64_t b, int64_t a,
+                         const double* rhs, int R, double* partial,
+                         int nchunks, double* rn, cudaStream_t s);
+// y_i -= arrow[i]^T * x_n for all i.
+cudaError_t arrow_scatter(const double* arrow, int64_t n, int64_t b, int64_t a,
+                          const double* xn, int R, double* rhs, cudaStream_t s);
+int arrow_chunks(int64_t n);
+
+// DMMA peak probe; *flops receives the launch's flop count.
+cudaError_t fp64_probe(double* out, long long iters, double* flops, cudaStream_t s);
+
+// Per-device info word (first failed pivot, LAPACK-style 1-based global row).
+cudaError_t info_reset(cudaStream_t s);
+cudaError_t info_read_reset(cudaStream_t s, long long* out);
+
+}  // namespace bta

@@ -1,0 +1,729 @@
+// FP64 kernels of the BTA path for sm_103a.
+//
+// On this part the FP64 pipe (DMMA and DFMA alike) is the bound: HBM and
+// shared-memory traffic of these kernels are two orders of magnitude below
+// their limits. So every kernel is written to keep the FP64 pipe of all SMs
+// busy: dense contractions go through warp-level DMMA (mma.sync m8n8k4 f64) on
+// 32x32 output tiles, many small CTAs are resident per SM, and triangular
+// operands skip the k-range that is known to be zero.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "bta_internal.cuh"
+#include "timing.cuh"
+
+namespace bta {
+
+// ---------------------------------------------------------------------------
+// Per-device info word: 1-based global row of the first non-positive pivot.
+// ---------------------------------------------------------------------------
+__device__ unsigned long long g_info;
+
+__device__ __forceinline__ void record_failure(long long row) {
+  atomicCAS(&g_info, 0ull, (unsigned long long)row);
+}
+
+cudaError_t info_reset(cudaStream_t s) {
+  static const unsigned long long zero = 0;
+  return cudaMemcpyToSymbolAsync(g_info, &zero, sizeof(zero), 0,
+                                 cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t info_read_reset(cudaStream_t s, long long* out) {
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_info, sizeof(v), 0,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  *out = (long long)v;
+  return info_reset(s);
+}
+
+// ---------------------------------------------------------------------------
+// DMMA tile GEMM: C = beta*C + sum_t alpha_t op(A_t) op(B_t).
+// 128 threads, one 32x32 output tile per CTA, each warp a 16x16 quadrant made
+// of 2x2 m8n8k4 fragments. Operands are staged through shared memory in 32-deep
+// k-chunks; ragged edges are zero-filled.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
+  asm volatile(
+      "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, "
+      "{%0,%1};\n"
+      : "+d"(c[0]), "+d"(c[1])
+      : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ double scale_by(double v, double alpha) {
+  if (alpha == 1.0) return v;
+  if (alpha == -1.0)
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+  return alpha * v;
+}
+
+__global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
+  __shared__ double As[T][T + 1];  // [m][k]
+  __shared__ double Bs[T][T + 1];  // [k][n]
+  const int tilesN = (g.N + T - 1) / T;
+  const int tilesM = (g.M + T - 1) / T;
+  long long bid = blockIdx.x;
+  const int tn = (int)(bid % tilesN);
+  bid /= tilesN;
+  const int tm = (int)(bid % tilesM);
+  bid /= tilesM;
+  const int z1 = (int)(bid % g.nb1);
+  const int z2 = (int)(bid / g.nb1);
+  if (g.lowerC && tn > tm) return;
+  const int m0 = tm * T, n0 = tn * T;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int wm = (warp >> 1) * 16, wn = (warp & 1) * 16;
+
+  double acc[2][2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+  for (int ti = 0; ti < g.nterms; ++ti) {
+    const GemmTerm& t = g.t[ti];
+    const double* A = t.A + (int64_t)z1 * t.sA1 + (int64_t)z2 * t.sA2;
+    const double* B = t.B + (int64_t)z1 * t.sB1 + (int64_t)z2 * t.sB2;
+    int kb = 0, ke = t.K;
+    if (t.triA == TRI_LOWER) ke = min(ke, m0 + T);
+    if (t.triA == TRI_UPPER) kb = max(kb, m0);
+    if (t.triB == TRI_LOWER) kb = max(kb, n0);
+    if (t.triB == TRI_UPPER) ke = min(ke, n0 + T);
+    for (int k0 = kb; k0 < ke; k0 += T) {
+      for (int e = tid; e < T * T; e += 128) {
+        int i, kk;
+        double v = 0.0;
+        if (t.opA == OP_N) {
+          i = e / T; kk = e % T;
+          const int gi = m0 + i, gk = k0 + kk;
+          if (gi < g.M && gk < ke) v = A[(int64_t)gi * t.lda + gk];
+        } else {
+          kk = e / T; i = e % T;
+          const int gi = m0 + i, gk = k0 + kk;
+          if (gi < g.M && gk < ke) v = A[(int64_t)gk * t.lda + gi];
+        }
+        As[i][kk] = scale_by(v, t.alpha);
+      }
+      for (int e = tid; e < T * T; e += 128) {
+        int kk, j;
+        double v = 0.0;
+        if (t.opB == OP_N) {
+          kk = e / T; j = e % T;
+          const int gk = k0 + kk, gj = n0 + j;
+          if (gk < ke && gj < g.N) v = B[(int64_t)gk * t.ldb + gj];
+        } else {
+          j = e / T; kk = e % T;
+          const int gk = k0 + kk, gj = n0 + j;
+          if (gk < ke && gj < g.N) v = B[(int64_t)gj * t.ldb + gk];
+        }
+        Bs[kk][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int ks = 0; ks < T; ks += 4) {
+        const double a0 = As[wm + gq][ks + tq];
+        const double a1 = As[wm + 8 + gq][ks + tq];
+        const double b0 = Bs[ks + tq][wn + gq];
+        const double b1 = Bs[ks + tq][wn + 8 + gq];
+        dmma_8x8x4(acc[0][0], a0, b0);
+        dmma_8x8x4(acc[0][1], a0, b1);
+        dmma_8x8x4(acc[1][0], a1, b0);
+        dmma_8x8x4(acc[1][1], a1, b1);
+      }
+      __syncthreads();
+    }
+  }
+
+  double* C = g.C + (int64_t)z1 * g.sC1 + (int64_t)z2 * g.sC2;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int r = m0 + wm + mi * 8 + gq;
+        const int c = n0 + wn + ni * 8 + 2 * tq + j;
+        if (r < g.M && c < g.N) {
+          double* p = C + (int64_t)r * g.ldc + c;
+          double v = acc[mi][ni][j];
+          if (g.beta != 0.0) v += g.beta * *p;
+          *p = v;
+        }
+      }
+}
+
+// Algorithmic flops of one launch: 2 per multiply-add whose operands are not
+// structurally zero, over the output elements the call defines (all of C, or
+// its lower triangle for lowerC). Host-side, only evaluated when timing is on.
+static double gemm_alg_flops(const GemmArgs& g) {
+  double total = 0.0;
+  for (int ti = 0; ti < g.nterms; ++ti) {
+    const GemmTerm& t = g.t[ti];
+    double cnt = 0.0;
+    if (t.triA == TRI_NONE && t.triB == TRI_NONE) {
+      double outs = 0.0;
+      if (g.lowerC)
+        for (int i = 0; i < g.M; ++i) outs += (double)min(i + 1, g.N);
+      else
+        outs = (double)g.M * g.N;
+      cnt = outs * t.K;
+    } else {
+      for (int i = 0; i < g.M; ++i) {
+        const int jn = g.lowerC ? min(i + 1, g.N) : g.N;
+        for (int j = 0; j < jn; ++j) {
+          int kb = 0, ke = t.K;
+          if (t.triA == TRI_LOWER) ke = min(ke, i + 1);
+          if (t.triA == TRI_UPPER) kb = max(kb, i);
+          if (t.triB == TRI_LOWER) kb = max(kb, j);
+          if (t.triB == TRI_UPPER) ke = min(ke, j + 1);
+          if (ke > kb) cnt += ke - kb;
+        }
+      }
+    }
+    total += 2.0 * cnt;
+  }
+  return total * g.nb1 * g.nb2;
+}
+
+cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
+  const long long tiles = (long long)((g.M + T - 1) / T) * ((g.N + T - 1) / T);
+  const long long grid = tiles * g.nb1 * g.nb2;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  TimedLaunch tl(K_GEMM, timing_on() ? gemm_alg_flops(g) : 0.0, s);
+  gemm_f64_kernel<<<(unsigned)grid, 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// POTRF of one diagonal tile; TRSM of the tiles below it; zeroing; mirroring.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, int64_t ld, int64_t sb,
+                                                         int nrow, int k, long long row0,
+                                                         long long rstride) {
+  __shared__ double S[T][T + 1];
+  __shared__ double rdiag;
+  double* Ab = A + (int64_t)blockIdx.y * sb;
+  const int o = k * T, tb = min(T, nrow - o), tid = threadIdx.x;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    S[i][j] = (i < tb && j <= i) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < tb; ++j) {
+    if (tid == 0) {
+      double d = S[j][j];
+      if (!(d > 0.0)) {
+        record_failure(row0 + (long long)blockIdx.y * rstride + o + j + 1);
+        d = __longlong_as_double(0x7ff8000000000000ll);  // NaN poisons what follows
+      }
+      d = sqrt(d);
+      S[j][j] = d;
+      rdiag = 1.0 / d;
+    }
+    __syncthreads();
+    const double r = rdiag;
+    for (int i = j + 1 + tid; i < tb; i += blockDim.x) S[i][j] *= r;
+    __syncthreads();
+    const int w = tb - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e / w, c = j + 1 + e % w;
+      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < tb * tb; e += blockDim.x) {
+    const int i = e / tb, j = e % tb;
+    Ab[(int64_t)(o + i) * ld + o + j] = (j <= i) ? S[i][j] : 0.0;
+  }
+}
+
+// Tiles (r, k) for r > k: X = A(r,k) L(k,k)^{-T}  (solve X L^T = A(r,k)).
+__global__ void __launch_bounds__(256) trsm_panel_kernel(double* A, int64_t ld, int64_t sb,
+                                                         int nrow, int k) {
+  __shared__ double Lk[T][T + 1];
+  __shared__ double X[T][T + 1];
+  __shared__ double rd[T];
+  double* Ab = A + (int64_t)blockIdx.y * sb;
+  const int o = k * T, tb = min(T, nrow - o);
+  const int r0 = o + T * (1 + blockIdx.x), rows = min(T, nrow - r0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    Lk[i][j] = (i < tb && j < tb) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
+    X[i][j] = (i < rows && j < tb) ? Ab[(int64_t)(r0 + i) * ld + o + j] : 0.0;
+  }
+  __syncthreads();
+  if (tid < tb) rd[tid] = 1.0 / Lk[tid][tid];
+  __syncthreads();
+  for (int j = 0; j < tb; ++j) {
+    for (int i = tid; i < rows; i += blockDim.x) X[i][j] *= rd[j];
+    __syncthreads();
+    const int w = tb - j - 1;
+    for (int e = tid; e < rows * w; e += blockDim.x) {
+      const int i = e / w, c = j + 1 + e % w;
+      X[i][c] -= X[i][j] * Lk[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < rows * tb; e += blockDim.x) {
+    const int i = e / tb, j = e % tb;
+    Ab[(int64_t)(r0 + i) * ld + o + j] = X[i][j];
+  }
+}
+
+// Strict upper triangle -> 0 (tiles with tc >= tr).
+__global__ void zero_upper_kernel(double* A, int64_t ld, int64_t sb, int nrow) {
+  const int nt = (nrow + T - 1) / T;
+  const int tr = blockIdx.x / nt, tc = blockIdx.x % nt;
+  if (tc < tr) return;
+  double* Ab = A + (int64_t)blockIdx.y * sb;
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    const int i = tr * T + e / T, j = tc * T + e % T;
+    if (i < nrow && j < nrow && j > i) Ab[(int64_t)i * ld + j] = 0.0;
+  }
+}
+
+// A[j][i] = A[i][j] for i > j (tiles with tr >= tc; tile (tr,tc) written to (tc,tr)).
+__global__ void mirror_kernel(double* A, int64_t ld, int64_t sb, int nrow) {
+  __shared__ double S[T][T + 1];
+  const int nt = (nrow + T - 1) / T;
+  const int tr = blockIdx.x / nt, tc = blockIdx.x % nt;
+  if (tc > tr) return;
+  double* Ab = A + (int64_t)blockIdx.y * sb;
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T, gi = tr * T + i, gj = tc * T + j;
+    S[i][j] = (gi < nrow && gj < nrow) ? Ab[(int64_t)gi * ld + gj] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    const int j = e / T, i = e % T;  // write row tc*T+j, column tr*T+i
+    const int gi = tr * T + i, gj = tc * T + j;
+    if (gi < nrow && gj < nrow && gi > gj) Ab[(int64_t)gj * ld + gi] = S[i][j];
+  }
+}
+
+// Inverse of each diagonal tile of lower-triangular blocks into Linv.
+__global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t ldl, int64_t sl,
+                                                       double* Li, int64_t ldi, int64_t si,
+                                                       int nrow) {
+  __shared__ double Ls[T][T + 1];
+  __shared__ double X[T][T + 1];
+  __shared__ double rd[T];
+  const int o = blockIdx.x * T, tb = min(T, nrow - o), tid = threadIdx.x;
+  const double* Lb = L + (int64_t)blockIdx.y * sl;
+  double* Xb = Li + (int64_t)blockIdx.y * si;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    Ls[i][j] = (i < tb && j <= i) ? Lb[(int64_t)(o + i) * ldl + o + j] : 0.0;
+    X[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid < tb) rd[tid] = 1.0 / Ls[tid][tid];
+  __syncthreads();
+  // Forward substitution on L X = I, row j of X at a time (columns <= j only).
+  for (int j = 0; j < tb; ++j) {
+    for (int c = tid; c <= j; c += blockDim.x) X[j][c] *= rd[j];
+    __syncthreads();
+    const int rows = tb - j - 1, cols = j + 1;
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+      const int i = j + 1 + e / cols, c = e % cols;
+      X[i][c] -= Ls[i][j] * X[j][c];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < tb * tb; e += blockDim.x) {
+    const int i = e / tb, j = e % tb;
+    Xb[(int64_t)(o + i) * ldi + o + j] = (j <= i) ? X[i][j] : 0.0;
+  }
+}
+
+static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
+                         long long info_row0, long long info_rstride, cudaStream_t s) {
+  if (count <= 0 || nrow <= 0) return cudaSuccess;
+  const int nt = (nrow + T - 1) / T;
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = min(65535, count - c0);
+    double* Ac = A + (int64_t)c0 * sb;
+    const long long r0 = info_row0 + (long long)c0 * info_rstride;
+    for (int k = 0; k < nt; ++k) {
+      {
+        TimedLaunch tl(K_POTRF_TILE, 0.0, s);
+        potrf_tile_kernel<<<dim3(1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k, r0, info_rstride);
+      }
+      if (k + 1 < nt) {
+        {
+          TimedLaunch tl(K_TRSM_PANEL, 0.0, s);
+          trsm_panel_kernel<<<dim3(nt - k - 1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k);
+        }
+        const int o = (k + 1) * T, m = nrow - o;
+        GemmArgs g{};
+        g.t[0] = term(Ac + (int64_t)o * ld + k * T, ld, OP_N, TRI_NONE,
+                      Ac + (int64_t)o * ld + k * T, ld, OP_T, TRI_NONE, T, -1.0);
+        g.t[0].sA1 = sb; g.t[0].sB1 = sb;
+        g.nterms = 1;
+        g.C = Ac + (int64_t)o * ld + o; g.ldc = ld; g.sC1 = sb;
+        g.M = m; g.N = m; g.beta = 1.0; g.lowerC = 1; g.nb1 = cnt; g.nb2 = 1;
+        cudaError_t e = gemm_f64(g, s);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    {
+      TimedLaunch tl(K_ZERO_UPPER, 0.0, s);
+      zero_upper_kernel<<<dim3(nt * nt, cnt), 256, 0, s>>>(Ac, ld, sb, nrow);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Li, int64_t ldi,
+                         int64_t si, int count, int nrow, cudaStream_t s) {
+  if (count <= 0 || nrow <= 0) return cudaSuccess;
+  const int nt = (nrow + T - 1) / T;
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = min(65535, count - c0);
+    const double* Lc = L + (int64_t)c0 * sl;
+    double* Xc = Li + (int64_t)c0 * si;
+    {
+      TimedLaunch tl(K_TILE_INV, 0.0, s);
+      tile_inv_kernel<<<dim3(nt, cnt), 256, 0, s>>>(Lc, ldl, sl, Xc, ldi, si, nrow);
+    }
+    // Doubling: [X11 0; X21 X22] with X21 = -X22 (L21 X11); the product
+    // (L21 X11)^T is parked in the (still unused) strict upper part.
+    for (int sz = T; sz < nrow; sz *= 2) {
+      const int full = nrow / (2 * sz);
+      const int tail_o = full * 2 * sz;
+      const int tail = (tail_o + sz < nrow) ? nrow - tail_o - sz : 0;
+      for (int part = 0; part < 2; ++part) {
+        const int pairs = part == 0 ? full : (tail ? 1 : 0);
+        if (!pairs) continue;
+        const int o = part == 0 ? 0 : tail_o;
+        const int s2 = part == 0 ? sz : tail;
+        const int64_t pstride_l = (int64_t)2 * sz * (ldl + 1);
+        const int64_t pstride_i = (int64_t)2 * sz * (ldi + 1);
+        // Tmp^T (sz x s2) = X11^T (sz x sz, upper) * L21^T (sz x s2)
+        GemmArgs g1{};
+        g1.t[0] = term(Xc + (int64_t)o * ldi + o, ldi, OP_T, TRI_UPPER,
+                       Lc + (int64_t)(o + sz) * ldl + o, ldl, OP_T, TRI_NONE, sz, 1.0);
+        g1.t[0].sA1 = pstride_i; g1.t[0].sB1 = pstride_l;
+        g1.t[0].sA2 = si; g1.t[0].sB2 = sl;
+        g1.nterms = 1;
+        g1.C = Xc + (int64_t)o * ldi + o + sz; g1.ldc = ldi; g1.sC1 = pstride_i; g1.sC2 = si;
+        g1.M = sz; g1.N = s2; g1.beta = 0.0; g1.lowerC = 0; g1.nb1 = pairs; g1.nb2 = cnt;
+        cudaError_t e = gemm_f64(g1, s);
+        if (e != cudaSuccess) return e;
+        // X21 (s2 x sz) = -X22 (s2 x s2, lower) * Tmp (s2 x sz)
+        GemmArgs g2{};
+        g2.t[0] = term(Xc + (int64_t)(o + sz) * ldi + o + sz, ldi, OP_N, TRI_LOWER,
+                       Xc + (int64_t)o * ldi + o + sz, ldi, OP_T, TRI_NONE, s2, -1.0);
+        g2.t[0].sA1 = pstride_i; g2.t[0].sB1 = pstride_i;
+        g2.t[0].sA2 = si; g2.t[0].sB2 = si;
+        g2.nterms = 1;
+        g2.C = Xc + (int64_t)(o + sz) * ldi + o; g2.ldc = ldi; g2.sC1 = pstride_i; g2.sC2 = si;
+        g2.M = s2; g2.N = sz; g2.beta = 0.0; g2.lowerC = 0; g2.nb1 = pairs; g2.nb2 = cnt;
+        e = gemm_f64(g2, s);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    {
+      TimedLaunch tl(K_ZERO_UPPER, 0.0, s);
+      zero_upper_kernel<<<dim3(nt * nt, cnt), 256, 0, s>>>(Xc, ldi, si, nrow);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mirror_lower(double* A, int64_t ld, int64_t sb, int count, int nrow, cudaStream_t s) {
+  if (count <= 0 || nrow <= 0) return cudaSuccess;
+  const int nt = (nrow + T - 1) / T;
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = min(65535, count - c0);
+    TimedLaunch tl(K_MIRROR, 0.0, s);
+    mirror_kernel<<<dim3(nt * nt, cnt), 256, 0, s>>>(A + (int64_t)c0 * sb, ld, sb, nrow);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// log-determinant: per-block sums in a fixed tree order, then blocks in order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) logdet_partial_kernel(const double* diag, int64_t n,
+                                                             int64_t b, const double* tip,
+                                                             int64_t a, double* partial) {
+  __shared__ double red[256];
+  const int64_t z = blockIdx.x;
+  const double* M = z < n ? diag + z * b * b : tip;
+  const int64_t m = z < n ? b : a;
+  double sum = 0.0;
+  for (int64_t k = threadIdx.x; k < m; k += 256) sum += log(M[k * m + k]);
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[z] = red[0];
+}
+
+__global__ void logdet_final_kernel(const double* partial, int64_t count, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int64_t z = 0; z < count; ++z) s += partial[z];
+    *out = 2.0 * s;
+  }
+}
+
+cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b, const double* tip, int64_t a,
+                       double* partial, double* out, cudaStream_t s) {
+  const int64_t count = n + (a > 0 ? 1 : 0);
+  TimedLaunch tl(K_LOGDET, 0.0, s);
+  logdet_partial_kernel<<<(unsigned)count, 256, 0, s>>>(diag, n, b, tip, a, partial);
+  logdet_final_kernel<<<1, 32, 0, s>>>(partial, count, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Solve pieces.
+// ---------------------------------------------------------------------------
+// In-place triangular solve with one CTA: L x = r (trans = false) or L^T x = r.
+__global__ void __launch_bounds__(512) trsv_kernel(const double* L, int64_t ld, int nrow,
+                                                   double* x, int64_t ldx, int R, int trans) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nt = (nrow + T - 1) / T;
+  for (int step = 0; step < nt; ++step) {
+    const int k = trans ? nt - 1 - step : step;
+    const int o = k * T, tb = min(T, nrow - o);
+    if (!trans) {
+      for (int j = o; j < o + tb; ++j) {
+        const double d = L[(int64_t)j * ld + j];
+        for (int r = tid; r < R; r += nth) x[(int64_t)j * ldx + r] /= d;
+        __syncthreads();
+        const int rows = o + tb - j - 1;
+        for (int e = tid; e < rows * R; e += nth) {
+          const int i = j + 1 + e / R, r = e % R;
+          x[(int64_t)i * ldx + r] -= L[(int64_t)i * ld + j] * x[(int64_t)j * ldx + r];
+        }
+        __syncthreads();
+      }
+      const int rows = nrow - (o + tb);
+      for (int e = tid; e < rows * R; e += nth) {
+        const int i = o + tb + e / R, r = e % R;
+        double acc = x[(int64_t)i * ldx + r];
+        for (int c = o; c < o + tb; ++c) acc -= L[(int64_t)i * ld + c] * x[(int64_t)c * ldx + r];
+        x[(int64_t)i * ldx + r] = acc;
+      }
+      __syncthreads();
+    } else {
+      for (int j = o + tb - 1; j >= o; --j) {
+        const double d = L[(int64_t)j * ld + j];
+        for (int r = tid; r < R; r += nth) x[(int64_t)j * ldx + r] /= d;
+        __syncthreads();
+        const int rows = j - o;
+        for (int e = tid; e < rows * R; e += nth) {
+          const int i = o + e / R, r = e % R;
+          x[(int64_t)i * ldx + r] -= L[(int64_t)j * ld + i] * x[(int64_t)j * ldx + r];
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < o * R; e += nth) {
+        const int i = e / R, r = e % R;
+        double acc = x[(int64_t)i * ldx + r];
+        for (int c = o; c < o + tb; ++c) acc -= L[(int64_t)c * ld + i] * x[(int64_t)c * ldx + r];
+        x[(int64_t)i * ldx + r] = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t ldx, int R,
+                       bool trans, cudaStream_t s) {
+  if (nrow <= 0) return cudaSuccess;
+  TimedLaunch tl(K_TRSV, 0.0, s);
+  trsv_kernel<<<1, 512, 0, s>>>(L, ld, nrow, x, ldx, R, trans ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// x[M][R] += alpha * A[M][K] y[K][R]: one warp per row, lanes over k, fixed-order
+// shuffle reduction. R is processed 8 columns at a time.
+__global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t lda, int M, int K,
+                                                     const double* y, int64_t ldy, double* x,
+                                                     int64_t ldx, int R, double alpha) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= M) return;
+  for (int r0 = 0; r0 < R; r0 += 8) {
+    const int rc = min(8, R - r0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      const double av = A[(int64_t)row * lda + k];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < rc) acc[q] += av * y[(int64_t)k * ldy + r0 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = acc[q];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      acc[q] = v;
+    }
+    if (lane == 0)
+      for (int q = 0; q < rc; ++q) x[(int64_t)row * ldx + r0 + q] += alpha * acc[q];
+  }
+}
+
+// x[M][R] += alpha * A^T y with A stored K x M: 32 rows per CTA (lane = row),
+// 8 warps split k and are summed in a fixed order.
+__global__ void __launch_bounds__(256) gemv_t_kernel(const double* A, int64_t lda, int M, int K,
+                                                     const double* y, int64_t ldy, double* x,
+                                                     int64_t ldx, int R, double alpha) {
+  __shared__ double red[8][32][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + lane;
+  const int kchunk = (K + 7) / 8, kb = w * kchunk, ke = min(K, kb + kchunk);
+  for (int r0 = 0; r0 < R; r0 += 8) {
+    const int rc = min(8, R - r0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    if (row < M)
+      for (int k = kb; k < ke; ++k) {
+        const double av = A[(int64_t)k * lda + row];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < rc) acc[q] += av * y[(int64_t)k * ldy + r0 + q];
+      }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[w][lane][q] = acc[q];
+    __syncthreads();
+    if (w == 0 && row < M) {
+      for (int q = 0; q < rc; ++q) {
+        double v = 0.0;
+        for (int ww = 0; ww < 8; ++ww) v += red[ww][lane][q];
+        x[(int64_t)row * ldx + r0 + q] += alpha * v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K, const double* y,
+                       int64_t ldy, double* x, int64_t ldx, int R, double alpha, cudaStream_t s) {
+  if (M <= 0 || K <= 0 || R <= 0) return cudaSuccess;
+  TimedLaunch tl(K_GEMV, 2.0 * M * K * R, s);
+  if (opA == OP_N)
+    gemv_n_kernel<<<ceil_div(M, 8), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
+  else
+    gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
+  return cudaGetLastError();
+}
+
+int arrow_chunks(int64_t n) { return (int)(n < 256 ? n : 256); }
+
+// partial[chunk][p][r] = sum over blocks i of the chunk of arrow[i][p][:] . y_i[:][r]
+__global__ void __launch_bounds__(256) arrow_gather_kernel(const double* arrow, int64_t n,
+                                                           int64_t b, int64_t a,
+                                                           const double* rhs, int R,
+                                                           double* partial, int nchunks) {
+  __shared__ double red[256];
+  const int64_t per = (n + nchunks - 1) / nchunks;
+  const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+  for (int64_t p = 0; p < a; ++p)
+    for (int r = 0; r < R; ++r) {
+      double sum = 0.0;
+      for (int64_t i = i0; i < i1; ++i)
+        for (int64_t j = threadIdx.x; j < b; j += 256)
+          sum += arrow[(i * a + p) * b + j] * rhs[(i * b + j) * R + r];
+      red[threadIdx.x] = sum;
+      __syncthreads();
+      for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) partial[((int64_t)blockIdx.x * a + p) * R + r] = red[0];
+      __syncthreads();
+    }
+}
+
+__global__ void arrow_gather_final_kernel(const double* partial, int nchunks, int64_t a, int R,
+                                          double* rn) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a * R) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(int64_t)c * a * R + e];
+  rn[e] -= s;
+}
+
+cudaError_t arrow_gather(const double* arrow, int64_t n, int64_t b, int64_t a, const double* rhs,
+                         int R, double* partial, int nchunks, double* rn, cudaStream_t s) {
+  if (a <= 0) return cudaSuccess;
+  TimedLaunch tl(K_ARROW, 2.0 * n * a * b * R, s);
+  arrow_gather_kernel<<<nchunks, 256, 0, s>>>(arrow, n, b, a, rhs, R, partial, nchunks);
+  arrow_gather_final_kernel<<<ceil_div(a * R, 128), 128, 0, s>>>(partial, nchunks, a, R, rn);
+  return cudaGetLastError();
+}
+
+// rhs[i*b + j][r] -= sum_p arrow[i][p][j] * xn[p][r]
+__global__ void arrow_scatter_kernel(const double* arrow, int64_t n, int64_t b, int64_t a,
+                                     const double* xn, int R, double* rhs) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * b) return;
+  const int64_t i = e / b, j = e % b;
+  for (int r = 0; r < R; ++r) {
+    double acc = 0.0;
+    for (int64_t p = 0; p < a; ++p) acc += arrow[(i * a + p) * b + j] * xn[p * R + r];
+    rhs[e * R + r] -= acc;
+  }
+}
+
+cudaError_t arrow_scatter(const double* arrow, int64_t n, int64_t b, int64_t a, const double* xn,
+                          int R, double* rhs, cudaStream_t s) {
+  if (a <= 0) return cudaSuccess;
+  TimedLaunch tl(K_ARROW, 2.0 * n * a * b * R, s);
+  arrow_scatter_kernel<<<ceil_div(n * b, 256), 256, 0, s>>>(arrow, n, b, a, xn, R, rhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 peak probe: independent DMMA m8n8k4 chains on every SM (the denominator
+// of the FP64 roofline, measured on the device that runs the path).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) fp64_probe_kernel(double* out, long long iters) {
+  double a = threadIdx.x * 1e-3, b = 0.999;
+  double c[4][2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) c[j][0] = c[j][1] = 0.0;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dmma_8x8x4(c[j], a, b);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r += c[j][0] + c[j][1];
+  if (r == 1234.5678) out[0] = r;  // never true; keeps the loop live
+}
+
+cudaError_t fp64_probe(double* out, long long iters, double* flops, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = 2 * sms, threads = 256;
+  *flops = 512.0 * 4.0 * (double)iters * blocks * (threads / 32);
+  TimedLaunch tl(K_PROBE, *flops, s);
+  fp64_probe_kernel<<<blocks, threads, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
+}  // namespace bta

@@ -1,0 +1,70 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol,
+sizes its workspaces, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bta.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|size_t)\s+(bta_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_17528_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2503_17528_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_lib.exported_symbols())
+
+
+def test_version(lib):
+    assert lib.bta_version() == 100
+
+
+def test_workspace_sizes(lib):
+    n, b, a = 365, 1024, 8
+    f = lib.bta_workspace_bytes(1, n, b, a, 1)
+    s = lib.bta_workspace_bytes(2, n, b, a, 1)
+    assert f >= 2 * b * b * 8 + a * b * 8
+    assert s >= (2 * n - 1) * b * b * 8 + n * a * b * 8
+    assert lib.bta_workspace_bytes(3, n, b, a, 4) > 0
+    assert lib.bta_workspace_bytes(4, n, b, a, 1) >= (n + 1) * 8
+    assert lib.bta_workspace_bytes(9, n, b, a, 1) == 0
+    assert lib.bta_workspace_bytes(1, 0, b, a, 1) == 0
+    assert lib.bta_workspace_bytes(3, n, b, a, 65) == 0
+
+
+def test_argument_errors_need_no_gpu(lib):
+    v = ctypes.c_void_p
+    good = v(4096)
+    assert lib.bta_factor(0, 4, 1, good, good, good, good, None) == -1
+    assert lib.bta_factor(2, 0, 1, good, good, good, good, None) == -2
+    assert lib.bta_factor(2, 4, -1, good, good, good, good, None) == -3
+    assert lib.bta_factor(2, 4, 1, None, good, good, good, None) == -4
+    assert lib.bta_factor(2, 4, 1, v(4097), good, good, good, None) == -4
+    assert lib.bta_factor(2, 4, 1, good, None, good, good, None) == -5
+    assert lib.bta_factor(2, 4, 1, good, good, None, good, None) == -6
+    assert lib.bta_factor(2, 4, 1, good, good, good, None, None) == -7
+    assert lib.bta_selinv(2, 4, 1, good, good, good, None, None) == -7
+    assert lib.bta_solve(2, 4, 1, good, good, good, good, None, 1, None) == -8
+    assert lib.bta_solve(2, 4, 1, good, good, good, good, good, 0, None) == -9
+    assert lib.bta_logdet(2, 4, 1, good, good, None, None) == -6
+    assert lib.bta_factor_ws(2, 4, 1, good, good, good, good, None, 0, None) == -8
+    assert lib.bta_factor_ws(2, 4, 1, good, good, good, good, v(4096), 16, None) == -9
+    assert lib.bta_get_info(None, None) == -2
