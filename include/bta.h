@@ -136,6 +136,23 @@ int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag,
                   const double* tip, double* out_dev, void* ws, size_t ws_bytes,
                   bta_stream_t stream);
 
+/*
+ * bta_logdet_noalloc -- the same result as bta_logdet, for callers that cannot
+ * allocate device memory when they need it (a host framework that owns the
+ * device-memory budget, or a latency-critical loop where cudaMalloc/cudaFree
+ * would synchronize the device). It allocates nothing: its scratch is a fixed
+ * 512 KiB array inside the library, present on every GPU that loads the library
+ * until the process exits. The paper has no counterpart; this is an interface
+ * convenience.
+ * Limits: n <= 65536 (larger n returns -1, nothing is enqueued).
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. All calls on
+ * a device share the array: calls that overlap on the GPU race and must be
+ * ordered by the caller (same stream, or events).
+ */
+int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double* diag,
+                       const double* tip, double* out_dev, bta_stream_t stream);
+
 /* ---- Measurement support (not part of the method) ----------------------- */
 
 /* Kernel ids for bta_timing_read. */

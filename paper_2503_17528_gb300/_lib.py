@@ -27,6 +27,7 @@ _SIGS = {
     "bta_selinv_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _sz, _p],
     "bta_solve_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _sz, _p],
     "bta_logdet_ws": [_i64, _i64, _i64, _p, _p, _p, _p, _sz, _p],
+    "bta_logdet_noalloc": [_i64, _i64, _i64, _p, _p, _p, _p],
     "bta_timing_enable": [ctypes.c_int],
     "bta_timing_read": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(_i64)],
