@@ -73,12 +73,24 @@ class ClockSampler:
         self.lines = []
         self.thread = None
 
+    @staticmethod
+    def _die_with_parent():
+        # The sampler must never outlive the benchmark (a profiler waits for
+        # every process of the tree): ask the kernel to SIGTERM it when the
+        # parent exits.
+        try:
+            import signal
+            ctypes.CDLL("libc.so.6", use_errno=True).prctl(1, signal.SIGTERM)  # PR_SET_PDEATHSIG
+        except Exception:
+            pass
+
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["timeout", "900", "nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                preexec_fn=self._die_with_parent)
         except OSError:
             self.proc = None
             return
@@ -225,7 +237,8 @@ def run_ours(args, w, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     barrier()
     torch.cuda.synchronize(dev)
-    sampler.start()
+    if not args.no_clocks:
+        sampler.start()
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -290,6 +303,23 @@ def run_ours(args, w, rank, world, local_rank):
         # Kernel-level measurement pass (after the timed steps): per-launch events
         # around every library kernel of one step, then the FP64 DMMA peak probe.
         stream = torch.cuda.current_stream(dev)
+        # Phase split of one step (events between the C calls on the stream).
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for dst, src in zip(W, P):
+            dst.copy_(src, non_blocking=True)
+        D, Lo, Ar, Ti, R = W
+        ev[0].record()
+        bta.factor(D, Lo, Ar, Ti)
+        ev[1].record()
+        bta.logdet(D, Ti, out=ld_out)
+        ev[2].record()
+        bta.solve(D, Lo, Ar, Ti, R)
+        ev[3].record()
+        bta.selinv(D, Lo, Ar, Ti)
+        ev[4].record()
+        torch.cuda.synchronize(dev)
+        phases = {nm: round(ev[i].elapsed_time(ev[i + 1]), 3)
+                  for i, nm in enumerate(["factor", "logdet", "solve", "selinv"])}
         lib.bta_timing_enable(1)
         step()
         torch.cuda.synchronize(dev)
@@ -335,6 +365,7 @@ def run_ours(args, w, rank, world, local_rank):
                 "avg_launch_ms": round(g_ms / max(g_cnt, 1), 5),
             },
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()},
+            "phase_ms": phases,
             "gpu_launches": int(launches_per_step * args.steps),
             "e2e": e2e,
         }
@@ -359,6 +390,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n365_b1024_a8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     ap.add_argument("--cpu-target-s", type=float, default=10.0)
     ap.add_argument("--ref-target-s", type=float, default=5.0)
     args = ap.parse_args()

@@ -67,11 +67,28 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
   __shared__ double Bs[T][T + 1];  // [k][n]
   const int tilesN = (g.N + T - 1) / T;
   const int tilesM = (g.M + T - 1) / T;
+  // Tile order: lower-only outputs of a square C enumerate just the lower
+  // tiles; triangular operands put the tiles with the longest k-range first
+  // (largest-first keeps the tail of the launch short).
+  const bool tri_enum = g.lowerC && g.M == g.N;
+  const long long per_batch = tri_enum ? (long long)tilesM * (tilesM + 1) / 2
+                                       : (long long)tilesM * tilesN;
   long long bid = blockIdx.x;
-  const int tn = (int)(bid % tilesN);
-  bid /= tilesN;
-  const int tm = (int)(bid % tilesM);
-  bid /= tilesM;
+  const long long tidx = bid % per_batch;
+  bid /= per_batch;
+  int tm, tn;
+  if (tri_enum) {
+    int r = (int)((sqrt(8.0 * (double)tidx + 1.0) - 1.0) * 0.5);
+    while ((long long)(r + 1) * (r + 2) / 2 <= tidx) ++r;
+    while ((long long)r * (r + 1) / 2 > tidx) --r;
+    tm = r;
+    tn = (int)(tidx - (long long)r * (r + 1) / 2);
+  } else {
+    tn = (int)(tidx % tilesN);
+    tm = (int)(tidx / tilesN);
+    if (g.t[0].triB == TRI_UPPER) tn = tilesN - 1 - tn;
+    if (g.t[0].triA == TRI_LOWER) tm = tilesM - 1 - tm;
+  }
   const int z1 = (int)(bid % g.nb1);
   const int z2 = (int)(bid / g.nb1);
   if (g.lowerC && tn > tm) return;
@@ -193,7 +210,8 @@ static double gemm_alg_flops(const GemmArgs& g) {
 
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
-  const long long tiles = (long long)((g.M + T - 1) / T) * ((g.N + T - 1) / T);
+  const long long tm = (g.M + T - 1) / T, tn = (g.N + T - 1) / T;
+  const long long tiles = (g.lowerC && g.M == g.N) ? tm * (tm + 1) / 2 : tm * tn;
   const long long grid = tiles * g.nb1 * g.nb2;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   TimedLaunch tl(K_GEMM, timing_on() ? gemm_alg_flops(g) : 0.0, s);
@@ -204,31 +222,53 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // POTRF of one diagonal tile; TRSM of the tiles below it; zeroing; mirroring.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, int64_t ld, int64_t sb,
-                                                         int nrow, int k, long long row0,
-                                                         long long rstride) {
+
+// 1/sqrt(d) for d > 0 by Newton-Raphson on f(y) = 1/y^2 - d (y <- y (3 - d y^2) / 2),
+// seeded with the single-precision hardware estimate rsqrtf. Two steps take the
+// ~2^-23 seed error below FP64 rounding. Every dependent FP64 instruction is
+// expensive on this part, and this chain is about half the length of a
+// correctly rounded sqrt followed by a division; the pivot is then d * y.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  double y = (double)rsqrtf((float)d);
+  const double h = 0.5 * d;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+// One right-looking step k of a blocked Cholesky, fused: CTA 0 factors the
+// diagonal tile (k,k) and writes it back (recording a failed pivot); CTA q >= 1
+// factors the same tile in shared memory (redundantly, nothing written) and
+// then solves its row tile r = k + q: X L_kk^T = A(r,k).
+__global__ void __launch_bounds__(256) potrf_panel_kernel(double* A, int64_t ld, int64_t sb,
+                                                          int nrow, int k, long long row0,
+                                                          long long rstride) {
   __shared__ double S[T][T + 1];
-  __shared__ double rdiag;
+  __shared__ double X[T][T + 1];
+  __shared__ double rd[T];
   double* Ab = A + (int64_t)blockIdx.y * sb;
   const int o = k * T, tb = min(T, nrow - o), tid = threadIdx.x;
+  const bool diag_cta = blockIdx.x == 0;
+  const int r0 = o + T * blockIdx.x, rows = diag_cta ? 0 : min(T, nrow - r0);
   for (int e = tid; e < T * T; e += blockDim.x) {
     const int i = e / T, j = e % T;
     S[i][j] = (i < tb && j <= i) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
+    if (!diag_cta) X[i][j] = (i < rows && j < tb) ? Ab[(int64_t)(r0 + i) * ld + o + j] : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < tb; ++j) {
     if (tid == 0) {
       double d = S[j][j];
       if (!(d > 0.0)) {
-        record_failure(row0 + (long long)blockIdx.y * rstride + o + j + 1);
+        if (diag_cta) record_failure(row0 + (long long)blockIdx.y * rstride + o + j + 1);
         d = __longlong_as_double(0x7ff8000000000000ll);  // NaN poisons what follows
       }
-      d = sqrt(d);
-      S[j][j] = d;
-      rdiag = 1.0 / d;
+      const double y = rsqrt_newton(d);
+      S[j][j] = d * y;
+      rd[j] = y;
     }
     __syncthreads();
-    const double r = rdiag;
+    const double r = rd[j];
     for (int i = j + 1 + tid; i < tb; i += blockDim.x) S[i][j] *= r;
     __syncthreads();
     const int w = tb - j - 1;
@@ -238,37 +278,21 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, int64_t ld, 
     }
     __syncthreads();
   }
-  for (int e = tid; e < tb * tb; e += blockDim.x) {
-    const int i = e / tb, j = e % tb;
-    Ab[(int64_t)(o + i) * ld + o + j] = (j <= i) ? S[i][j] : 0.0;
+  if (diag_cta) {
+    for (int e = tid; e < tb * tb; e += blockDim.x) {
+      const int i = e / tb, j = e % tb;
+      Ab[(int64_t)(o + i) * ld + o + j] = (j <= i) ? S[i][j] : 0.0;
+    }
+    return;
   }
-}
-
-// Tiles (r, k) for r > k: X = A(r,k) L(k,k)^{-T}  (solve X L^T = A(r,k)).
-__global__ void __launch_bounds__(256) trsm_panel_kernel(double* A, int64_t ld, int64_t sb,
-                                                         int nrow, int k) {
-  __shared__ double Lk[T][T + 1];
-  __shared__ double X[T][T + 1];
-  __shared__ double rd[T];
-  double* Ab = A + (int64_t)blockIdx.y * sb;
-  const int o = k * T, tb = min(T, nrow - o);
-  const int r0 = o + T * (1 + blockIdx.x), rows = min(T, nrow - r0);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const int i = e / T, j = e % T;
-    Lk[i][j] = (i < tb && j < tb) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
-    X[i][j] = (i < rows && j < tb) ? Ab[(int64_t)(r0 + i) * ld + o + j] : 0.0;
-  }
-  __syncthreads();
-  if (tid < tb) rd[tid] = 1.0 / Lk[tid][tid];
-  __syncthreads();
+  // Row tile: X = A(r,k) L_kk^{-T}, column sweep (rd[j] = 1 / L_jj).
   for (int j = 0; j < tb; ++j) {
     for (int i = tid; i < rows; i += blockDim.x) X[i][j] *= rd[j];
     __syncthreads();
     const int w = tb - j - 1;
     for (int e = tid; e < rows * w; e += blockDim.x) {
       const int i = e / w, c = j + 1 + e % w;
-      X[i][c] -= X[i][j] * Lk[c][j];
+      X[i][c] -= X[i][j] * S[c][j];
     }
     __syncthreads();
   }
@@ -277,7 +301,6 @@ __global__ void __launch_bounds__(256) trsm_panel_kernel(double* A, int64_t ld, 
     Ab[(int64_t)(r0 + i) * ld + o + j] = X[i][j];
   }
 }
-
 // Strict upper triangle -> 0 (tiles with tc >= tr).
 __global__ void zero_upper_kernel(double* A, int64_t ld, int64_t sb, int nrow) {
   const int nt = (nrow + T - 1) / T;
@@ -357,13 +380,10 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
     for (int k = 0; k < nt; ++k) {
       {
         TimedLaunch tl(K_POTRF_TILE, 0.0, s);
-        potrf_tile_kernel<<<dim3(1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k, r0, info_rstride);
+        potrf_panel_kernel<<<dim3(nt - k, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k, r0,
+                                                             info_rstride);
       }
       if (k + 1 < nt) {
-        {
-          TimedLaunch tl(K_TRSM_PANEL, 0.0, s);
-          trsm_panel_kernel<<<dim3(nt - k - 1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k);
-        }
         const int o = (k + 1) * T, m = nrow - o;
         GemmArgs g{};
         g.t[0] = term(Ac + (int64_t)o * ld + k * T, ld, OP_N, TRI_NONE,
@@ -493,63 +513,137 @@ cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b, const double* t
 // ---------------------------------------------------------------------------
 // Solve pieces.
 // ---------------------------------------------------------------------------
-// In-place triangular solve with one CTA: L x = r (trans = false) or L^T x = r.
-__global__ void __launch_bounds__(512) trsv_kernel(const double* L, int64_t ld, int nrow,
-                                                   double* x, int64_t ldx, int R, int trans) {
-  const int tid = threadIdx.x, nth = blockDim.x;
+// In-place triangular solve L x = r (trans = 0) or L^T x = r (trans = 1) by one
+// thread-block cluster. Row tiles are owned round-robin by the cluster's CTAs.
+// Step k: the owner of tile k solves it (one warp per right-hand side, lanes =
+// rows, shuffles carry x_j down the tile), a cluster barrier (release/acquire)
+// publishes it, and every CTA subtracts its contribution from the row tiles it
+// owns that are still unsolved. The owner of tile k+1 has applied every update
+// to that tile itself, so one barrier per tile step suffices.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
+                                                           double* x, int64_t ldx, int R,
+                                                           int trans) {
+  __shared__ double Xk[T][65];
+  __shared__ double Lk[T][T + 1];
+  __shared__ double rdiag[T];
+  unsigned rank, csize;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = (nrow + T - 1) / T;
   for (int step = 0; step < nt; ++step) {
     const int k = trans ? nt - 1 - step : step;
     const int o = k * T, tb = min(T, nrow - o);
-    if (!trans) {
-      for (int j = o; j < o + tb; ++j) {
-        const double d = L[(int64_t)j * ld + j];
-        for (int r = tid; r < R; r += nth) x[(int64_t)j * ldx + r] /= d;
-        __syncthreads();
-        const int rows = o + tb - j - 1;
-        for (int e = tid; e < rows * R; e += nth) {
-          const int i = j + 1 + e / R, r = e % R;
-          x[(int64_t)i * ldx + r] -= L[(int64_t)i * ld + j] * x[(int64_t)j * ldx + r];
-        }
-        __syncthreads();
-      }
-      const int rows = nrow - (o + tb);
-      for (int e = tid; e < rows * R; e += nth) {
-        const int i = o + tb + e / R, r = e % R;
-        double acc = x[(int64_t)i * ldx + r];
-        for (int c = o; c < o + tb; ++c) acc -= L[(int64_t)i * ld + c] * x[(int64_t)c * ldx + r];
-        x[(int64_t)i * ldx + r] = acc;
+    if ((unsigned)(k % (int)csize) == rank) {
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, c = e % T;
+        Lk[i][c] = (i < tb && c <= i) ? L[(int64_t)(o + i) * ld + o + c] : 0.0;
       }
       __syncthreads();
-    } else {
-      for (int j = o + tb - 1; j >= o; --j) {
-        const double d = L[(int64_t)j * ld + j];
-        for (int r = tid; r < R; r += nth) x[(int64_t)j * ldx + r] /= d;
-        __syncthreads();
-        const int rows = j - o;
-        for (int e = tid; e < rows * R; e += nth) {
-          const int i = o + e / R, r = e % R;
-          x[(int64_t)i * ldx + r] -= L[(int64_t)j * ld + i] * x[(int64_t)j * ldx + r];
+      if (tid < tb) rdiag[tid] = 1.0 / Lk[tid][tid];
+      __syncthreads();
+      for (int q = warp; q < R; q += 8) {
+        double xi = lane < tb ? x[(int64_t)(o + lane) * ldx + q] : 0.0;
+        if (!trans) {
+          for (int j = 0; j < tb; ++j) {
+            const double xj = __shfl_sync(0xffffffffu, xi, j) * rdiag[j];
+            if (lane == j) xi = xj;
+            else if (lane > j) xi -= Lk[lane][j] * xj;
+          }
+        } else {
+          for (int j = tb - 1; j >= 0; --j) {
+            const double xj = __shfl_sync(0xffffffffu, xi, j) * rdiag[j];
+            if (lane == j) xi = xj;
+            else if (lane < j) xi -= Lk[j][lane] * xj;
+          }
         }
-        __syncthreads();
+        if (lane < tb) x[(int64_t)(o + lane) * ldx + q] = xi;
       }
-      for (int e = tid; e < o * R; e += nth) {
-        const int i = e / R, r = e % R;
-        double acc = x[(int64_t)i * ldx + r];
-        for (int c = o; c < o + tb; ++c) acc -= L[(int64_t)c * ld + i] * x[(int64_t)c * ldx + r];
-        x[(int64_t)i * ldx + r] = acc;
+    }
+    cluster_sync_all();
+    for (int e = tid; e < tb * R; e += blockDim.x) Xk[e / R][e % R] = x[(int64_t)(o + e / R) * ldx + e % R];
+    __syncthreads();
+    for (int r = (int)rank; r < nt; r += (int)csize) {
+      if ((!trans && r <= k) || (trans && r >= k)) continue;
+      const int ro = r * T, rb = min(T, nrow - ro);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        if (!trans) {
+          const int i = e / T, c = e % T;
+          Lk[i][c] = (i < rb && c < tb) ? L[(int64_t)(ro + i) * ld + o + c] : 0.0;
+        } else {
+          const int c = e / T, i = e % T;  // L[o+c][ro+i] = (L^T)[ro+i][o+c]
+          Lk[i][c] = (i < rb && c < tb) ? L[(int64_t)(o + c) * ld + ro + i] : 0.0;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < rb * R; e += blockDim.x) {
+        const int i = e / R, q = e % R;
+        double acc = 0.0;
+        for (int c = 0; c < tb; ++c) acc += Lk[i][c] * Xk[c][q];
+        x[(int64_t)(ro + i) * ldx + q] -= acc;
       }
       __syncthreads();
     }
   }
 }
 
+static int trsv_cluster_size(cudaStream_t s) {
+  static int chosen = 0;
+  if (chosen) return chosen;
+  int sz = 16;
+  if (cudaFuncSetAttribute(trsv_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    sz = 8;
+  }
+  if (sz == 16) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, trsv_cluster_kernel, &cfg) != cudaSuccess ||
+        nclusters < 1) {
+      cudaGetLastError();
+      sz = 8;
+    }
+  }
+  chosen = sz;
+  return chosen;
+}
+
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t ldx, int R,
                        bool trans, cudaStream_t s) {
   if (nrow <= 0) return cudaSuccess;
-  TimedLaunch tl(K_TRSV, 0.0, s);
-  trsv_kernel<<<1, 512, 0, s>>>(L, ld, nrow, x, ldx, R, trans ? 1 : 0);
-  return cudaGetLastError();
+  if (R > 64) return cudaErrorInvalidValue;
+  const int nt = (nrow + T - 1) / T;
+  int csize = trsv_cluster_size(s);
+  while (csize > 1 && csize > nt) csize /= 2;
+  TimedLaunch tl(K_TRSV, 2.0 * nrow * nrow * R / 2, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, x, ldx, R, trans ? 1 : 0);
 }
 
 // x[M][R] += alpha * A[M][K] y[K][R]: one warp per row, lanes over k, fixed-order
