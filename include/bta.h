@@ -153,6 +153,49 @@ int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag,
 int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double* diag,
                        const double* tip, double* out_dev, bta_stream_t stream);
 
+/* ---- Precision of the block products ------------------------------------ */
+
+#define BTA_PREC_FP64 0   /* FP64 DMMA (mma.sync f64) everywhere (default) */
+#define BTA_PREC_OZAKI 1  /* large products as FP64 emulated on BF16 tensor cores (tcgen05):
+                             7 BF16 digit slices per operand (Ozaki et al. 2012 splitting),
+                             exact FP32 accumulation of the leading slice-product groups;
+                             about 1e-13 relative error per product for k <= 1024 */
+#define BTA_PREC_BF16X3 2 /* mixed precision: the Schur-complement and inverse-recurrence
+                             products as split-BF16x3 (hi*hi + hi*lo + lo*hi) with FP32
+                             accumulation on tcgen05; POTRF, the triangular inverses and
+                             products, the tip and log-det stay FP64 */
+
+/*
+ * bta_set_precision -- selects how bta_factor and bta_selinv run their large
+ * block products (blocks of at least 64 x 64 with k >= 64; smaller ones always
+ * use FP64). Process-wide; set it before querying bta_workspace_bytes (the
+ * tensor-core modes need more scratch) and not while calls are in flight.
+ * Returns 0, or -1 for an unknown mode. Neither mode is part of the paper, whose
+ * computation is all FP64 (Section 5.2).
+ */
+int bta_set_precision(int prec);
+int bta_get_precision(void);
+
+/*
+ * bta_gemm -- C = alpha op(A) op(B) + beta C on one device, FP64 in and out,
+ * computed in precision `prec` (BTA_PREC_*). op(X) = X or X^T (trans != 0);
+ * row-major, M x N output. The dense block product every step of the method is
+ * built from, exported for direct use and testing. BTA_PREC_FP64 needs no
+ * workspace; the tensor-core modes need bta_gemm_workspace_bytes(prec, M, N, K)
+ * bytes of 256-byte aligned device scratch.
+ */
+size_t bta_gemm_workspace_bytes(int prec, int64_t M, int64_t N, int64_t K);
+int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+             int64_t lda, int transA, const double* B, int64_t ldb, int transB, double beta,
+             double* C, int64_t ldc, void* ws, size_t ws_bytes, bta_stream_t stream);
+
+/*
+ * bta_tc_status -- reads and clears the tensor-core kernels' timeout flag
+ * (1: a bounded wait inside a tcgen05 kernel gave up and its tile was not
+ * written; 0: none since the last read). Synchronous.
+ */
+int bta_tc_status(int* timed_out);
+
 /* ---- Measurement support (not part of the method) ----------------------- */
 
 /* Kernel ids for bta_timing_read. */
@@ -167,6 +210,7 @@ int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double* diag,
 #define BTA_KERNEL_GEMV 8
 #define BTA_KERNEL_ARROW 9
 #define BTA_KERNEL_PROBE 10
+#define BTA_KERNEL_GEMM_TC 11  /* tcgen05 BF16-slice GEMM (OZAKI / BF16X3 modes) */
 
 /*
  * bta_timing_enable -- on != 0: from now on every kernel launch of the library

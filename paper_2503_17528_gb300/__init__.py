@@ -11,13 +11,20 @@ from __future__ import annotations
 from .api import (  # noqa: F401
     BTAError,
     OP_FACTOR,
+    PREC_BF16X3,
+    PREC_FP64,
+    PREC_OZAKI,
     OP_LOGDET,
     OP_SELINV,
     OP_SOLVE,
     factor,
+    gemm,
     get_info,
+    get_precision,
     logdet,
     selinv,
+    set_precision,
     solve,
+    tc_status,
     workspace_bytes,
 )

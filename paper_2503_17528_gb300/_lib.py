@@ -32,6 +32,12 @@ _SIGS = {
     "bta_timing_read": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(_i64)],
     "bta_probe_fp64_peak": [_p, _i64, ctypes.POINTER(ctypes.c_double), _p],
+    "bta_set_precision": [ctypes.c_int],
+    "bta_get_precision": [],
+    "bta_gemm_workspace_bytes": [ctypes.c_int, _i64, _i64, _i64],
+    "bta_gemm": [ctypes.c_int, _i64, _i64, _i64, ctypes.c_double, _p, _i64, ctypes.c_int, _p, _i64,
+                 ctypes.c_int, ctypes.c_double, _p, _i64, _p, _sz, _p],
+    "bta_tc_status": [ctypes.POINTER(ctypes.c_int)],
     "bta_version": [],
 }
 
@@ -49,7 +55,7 @@ def load() -> ctypes.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = _sz if name == "bta_workspace_bytes" else ctypes.c_int
+        fn.restype = _sz if name.endswith("workspace_bytes") else ctypes.c_int
     _lib = lib
     return lib
 

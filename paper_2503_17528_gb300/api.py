@@ -129,3 +129,50 @@ def get_info(device=None) -> int:
     with torch.cuda.device(dev):
         _check(lib.bta_get_info(_stream(dev), ctypes.byref(v)), "bta_get_info")
     return int(v.value)
+
+
+PREC_FP64, PREC_OZAKI, PREC_BF16X3 = 0, 1, 2
+_PREC_NAMES = {"fp64": PREC_FP64, "ozaki": PREC_OZAKI, "bf16x3": PREC_BF16X3}
+
+
+def set_precision(prec) -> None:
+    """Precision of the large block products of factor/selinv: "fp64" (DMMA),
+    "ozaki" (FP64 emulated on BF16 tensor cores) or "bf16x3" (mixed)."""
+    p = _PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
+    _check(_lib.load().bta_set_precision(p), "bta_set_precision")
+
+
+def get_precision() -> int:
+    return int(_lib.load().bta_get_precision())
+
+
+def gemm(A, B, C=None, *, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, precision="fp64"):
+    """C = alpha op(A) op(B) + beta C through bta_gemm (FP64 tensors on one device)."""
+    p = _PREC_NAMES[precision] if isinstance(precision, str) else int(precision)
+    for t in (A, B):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2:
+            raise ValueError("A and B must be contiguous 2-D float64 CUDA tensors")
+    M = A.shape[1] if trans_a else A.shape[0]
+    K = A.shape[0] if trans_a else A.shape[1]
+    Kb = B.shape[1] if trans_b else B.shape[0]
+    N = B.shape[0] if trans_b else B.shape[1]
+    if K != Kb:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    lib = _lib.load()
+    with torch.cuda.device(A.device):
+        nbytes = int(lib.bta_gemm_workspace_bytes(p, M, N, K))
+        ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=A.device)
+        wp = ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+        _check(lib.bta_gemm(p, M, N, K, alpha, _ptr(A), A.shape[1], int(trans_a), _ptr(B), B.shape[1],
+                            int(trans_b), beta, _ptr(C), C.shape[1], wp, nbytes, _stream(A.device)),
+               "bta_gemm")
+    return C
+
+
+def tc_status() -> int:
+    """1 if a tensor-core kernel gave up on a bounded wait since the last read."""
+    v = ctypes.c_int(0)
+    _check(_lib.load().bta_tc_status(ctypes.byref(v)), "bta_tc_status")
+    return int(v.value)

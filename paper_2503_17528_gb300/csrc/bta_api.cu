@@ -5,6 +5,7 @@
 
 #include "../../include/bta.h"
 #include "bta_internal.cuh"
+#include "kernels_tc.cuh"
 
 using namespace bta;
 
@@ -32,8 +33,11 @@ struct Carver {
   }
 };
 
-struct FactorWs { double *Linv, *W, *Wa; };
-struct SelinvWs { double *Linv, *G, *H, *LtInv; };
+struct FactorWs { double *Linv, *W, *Wa; void* tc; size_t tc_bytes; };
+struct SelinvWs { double *Linv, *G, *H, *LtInv; void* tc; size_t tc_bytes; };
+
+extern int g_prec;
+size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch);
 struct SolveWs { double* partial; };
 struct LogdetWs { double* partial; };
 
@@ -44,6 +48,8 @@ size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o) {
   w.Linv = c.take((size_t)(b * b));
   w.W = c.take((size_t)(b * b));
   w.Wa = c.take((size_t)(a * b + 1));
+  w.tc_bytes = tc_bytes_for(b, a, 1);
+  w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
   if (o) *o = w;
   return c.off;
 }
@@ -55,6 +61,8 @@ size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o) {
   w.G = c.take((size_t)((n - 1) * b * b + 1));
   w.H = c.take((size_t)(n * a * b + 1));
   w.LtInv = c.take((size_t)(a * a + 1));
+  w.tc_bytes = tc_bytes_for(b, a, n);
+  w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
   if (o) *o = w;
   return c.off;
 }
@@ -109,10 +117,52 @@ GemmArgs one_term(const GemmTerm& t, double* C, int64_t ldc, int M, int N, doubl
   return g;
 }
 
+// Precision of the large block products (process-wide; see bta_set_precision).
+int g_prec = BTA_PREC_FP64;
+
+// Classes of GEMM call sites, to route them by precision mode.
+enum { CLS_SCHUR = 0, CLS_TRSM = 1, CLS_SELINV = 2 };
+
+int tc_mode_of(int prec) { return prec == BTA_PREC_OZAKI ? TC_OZ : (prec == BTA_PREC_BF16X3 ? TC_X3 : 0); }
+
+bool routes_to_tc(int prec, int cls) {
+  if (prec == BTA_PREC_OZAKI) return true;
+  if (prec == BTA_PREC_BF16X3) return cls == CLS_SCHUR || cls == CLS_SELINV;
+  return false;
+}
+
+bool tc_eligible(const GemmTerm& t, int M, int N) { return M >= 64 && N >= 64 && t.K >= 64; }
+
+struct TcWs {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Runs a (one- or two-term) GEMM: eligible terms on the tensor cores in the
+// current precision mode, the rest with the FP64 DMMA kernel (later terms
+// accumulate with beta = 1).
+cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, cudaStream_t s) {
+  const int prec = g_prec;
+  if (prec == BTA_PREC_FP64 || !routes_to_tc(prec, cls) || !tw.p) return gemm_f64(g, s);
+  for (int i = 0; i < g.nterms; ++i) {
+    GemmArgs gi = g;
+    gi.t[0] = g.t[i];
+    gi.nterms = 1;
+    if (i > 0) gi.beta = 1.0;
+    cudaError_t e = tc_eligible(gi.t[0], g.M, g.N) ? gemm_tc(gi, tc_mode_of(prec), tw.p, tw.bytes, s)
+                                                  : gemm_f64(gi, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
                 double* tip, const FactorWs& w, cudaStream_t s) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b;
+  TcWs tw;
+  tw.p = w.tc;
+  tw.bytes = w.tc_bytes;
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
     BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
@@ -120,28 +170,28 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     if (i + 1 < n) {
       double* Li = lower + i * bb;
       // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
-      BTA_TRY(gemm_f64(one_term(term(Li, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.W, b, B, B, 0.0, 0), s));
+      BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
+                                w.W, b, B, B, 0.0, 0), CLS_TRSM, tw, s));
       BTA_TRY(cudaMemcpyAsync(Li, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
       // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
-      BTA_TRY(gemm_f64(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
-                                Di + bb, b, B, B, 1.0, 1), s));
+      BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
+                                Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, s));
     }
     if (a > 0) {
       double* Ai = arrow + i * a * b;
       // L_{n,i} = A_{n,i} L_ii^{-T}
-      BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.Wa, b, Aa, B, 0.0, 0), s));
+      BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
+                                w.Wa, b, Aa, B, 0.0, 0), CLS_TRSM, tw, s));
       BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
       if (i + 1 < n) {
         // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
-        BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, lower + i * bb, b, OP_T, TRI_NONE,
+        BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, lower + i * bb, b, OP_T, TRI_NONE,
                                        B, -1.0),
-                                  Ai + a * b, b, Aa, B, 1.0, 0), s));
+                                  Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, s));
       }
       // A_{n,n} -= L_{n,i} L_{n,i}^T
-      BTA_TRY(gemm_f64(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
-                                tip, a, Aa, Aa, 1.0, 1), s));
+      BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
+                                tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, s));
     }
   }
   if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
@@ -152,31 +202,34 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
                 double* tip, const SelinvWs& w, cudaStream_t s) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b, ab = a * b;
+  TcWs tw;
+  tw.p = w.tc;
+  tw.bytes = w.tc_bytes;
   // Prologue, independent over i: L_ii^{-1}, G_i, H_i, M_i; then X_nn.
   BTA_TRY(trtri_blocks(diag, b, bb, w.Linv, b, bb, (int)n, B, s));
   if (n > 1) {
     GemmArgs g = one_term(term(lower, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           w.G, b, B, B, 0.0, 0);
     g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)(n - 1);
-    BTA_TRY(gemm_f64(g, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
   }
   if (a > 0) {
     GemmArgs g = one_term(term(arrow, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           w.H, b, Aa, B, 0.0, 0);
     g.t[0].sA1 = ab; g.t[0].sB1 = bb; g.sC1 = ab; g.nb1 = (int)n;
-    BTA_TRY(gemm_f64(g, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
   }
   {
     GemmArgs g = one_term(term(w.Linv, b, OP_T, TRI_UPPER, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           diag, b, B, B, 0.0, 1);
     g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)n;
-    BTA_TRY(gemm_f64(g, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
   }
   if (a > 0) {
     BTA_TRY(trtri_blocks(tip, a, a * a, w.LtInv, a, a * a, 1, Aa, s));
-    BTA_TRY(gemm_f64(one_term(term(w.LtInv, a, OP_T, TRI_UPPER, w.LtInv, a, OP_N, TRI_LOWER, Aa,
+    BTA_TRY(gemm_run(one_term(term(w.LtInv, a, OP_T, TRI_UPPER, w.LtInv, a, OP_N, TRI_LOWER, Aa,
                                    1.0),
-                              tip, a, Aa, Aa, 0.0, 0), s));
+                              tip, a, Aa, Aa, 0.0, 0), CLS_SELINV, tw, s));
   }
   // Backward sweep.
   for (int64_t i = n - 1; i >= 0; --i) {
@@ -191,7 +244,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
     }
     if (a > 0) {
       // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i
@@ -201,7 +254,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
     }
     // X_ii = M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i  (lower tiles, then mirrored)
     GemmArgs g{};
@@ -210,7 +263,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       g.t[g.nterms++] = term(lower + i * bb, b, OP_T, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
     if (a > 0)
       g.t[g.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
-    if (g.nterms) BTA_TRY(gemm_f64(g, s));
+    if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
     BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
   }
   return 0;
@@ -254,6 +307,13 @@ int with_async_ws(size_t bytes, cudaStream_t s, F body) {
     if (rc == 0 && e != cudaSuccess) return (int)e;
   }
   return rc;
+}
+
+size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch) {
+  const int mode = tc_mode_of(g_prec);
+  if (!mode || b < 64) return 0;
+  const int m = (int)(a > b ? a : b);  // the widest product: b x b, or a x b / a x a blocks
+  return tc_workspace_bytes(mode, m, m, m, (int)(batch < 1 ? 1 : batch));
 }
 
 }  // namespace
@@ -384,6 +444,55 @@ int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,
   if (iters < 1) return -2;
   if (!flops) return -3;
   BTA_TRY(fp64_probe(out_dev, iters, flops, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_set_precision(int prec) {
+  if (prec != BTA_PREC_FP64 && prec != BTA_PREC_OZAKI && prec != BTA_PREC_BF16X3) return -1;
+  g_prec = prec;
+  return 0;
+}
+
+int bta_get_precision(void) { return g_prec; }
+
+size_t bta_gemm_workspace_bytes(int prec, int64_t M, int64_t N, int64_t K) {
+  const int mode = tc_mode_of(prec);
+  if (!mode || M < 1 || N < 1 || K < 1 || M > (1 << 30) || N > (1 << 30)) return 0;
+  if (K > 16384) return 0;
+  return tc_workspace_bytes(mode, (int)M, (int)N, (int)K, 1);
+}
+
+int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+             int transA, const double* B, int64_t ldb, int transB, double beta, double* C,
+             int64_t ldc, void* ws, size_t ws_bytes, bta_stream_t stream) {
+  if (prec != BTA_PREC_FP64 && prec != BTA_PREC_OZAKI && prec != BTA_PREC_BF16X3) return -1;
+  if (M < 1 || M > (1 << 30)) return -2;
+  if (N < 1 || N > (1 << 30)) return -3;
+  if (K < 1 || K > (1 << 30)) return -4;
+  if (!A || misaligned(A)) return -6;
+  if (lda < (transA ? M : K)) return -7;
+  if (!B || misaligned(B)) return -9;
+  if (ldb < (transB ? K : N)) return -10;
+  if (!C || misaligned(C)) return -13;
+  if (ldc < N) return -14;
+  GemmArgs g = one_term(term(A, lda, transA ? OP_T : OP_N, TRI_NONE, B, ldb, transB ? OP_T : OP_N,
+                             TRI_NONE, (int)K, alpha),
+                        C, ldc, (int)M, (int)N, beta, 0);
+  const int mode = tc_mode_of(prec);
+  if (!mode) {
+    BTA_TRY(gemm_f64(g, (cudaStream_t)stream));
+    return 0;
+  }
+  if (!ws || ((uintptr_t)ws % kAlign)) return -15;
+  if (K > 16384) return -4;
+  if (ws_bytes < tc_workspace_bytes(mode, (int)M, (int)N, (int)K, 1)) return -16;
+  BTA_TRY(gemm_tc(g, mode, ws, ws_bytes, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_tc_status(int* timed_out) {
+  if (!timed_out) return -1;
+  BTA_TRY(tc_error_read_reset(timed_out));
   return 0;
 }
 

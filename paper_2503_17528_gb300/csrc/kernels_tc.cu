@@ -1,0 +1,705 @@
+// Tensor-core GEMM for the BTA path on sm_103a: FP64 operands are split into
+// BF16 slices and multiplied on the 5th-generation tensor cores (tcgen05,
+// kind::f16, FP32 accumulation in TMEM), operands staged by TMA.
+//
+// Two splittings share one kernel:
+//  * OZ (FP64-class): the error-free splitting of Ozaki et al. (2012). Every row
+//    of op(A) (column of op(B)) gets a power-of-two scale 2^e with all entries
+//    below 2^(e-1); the scaled value is rounded to a 7*s-bit integer Y and cut
+//    into s balanced base-128 digits d_1..d_s (|d_1| <= 65, |d_p| <= 64), stored
+//    as BF16 values d_p * 2^-7p (exact). Products of digit slices p, q are
+//    grouped by d = p + q: groups d = 2..6 each accumulate in their own FP32 TMEM
+//    accumulator over k-units of at most 512, where every partial sum is an
+//    integer multiple of 2^-7d below 2^24 of them (so it is exact whatever the
+//    accumulator's rounding mode); groups d >= 7 share one accumulator that sits
+//    2^-35 below the leading group. Pairs with d > s + 1 are dropped (triangular
+//    truncation). Each k-unit's groups are combined into one int64 fixed-point
+//    value (quantum 2^-49 of the scales) and summed with integer atomics, which
+//    makes the k split exact and the result independent of summation order; a
+//    finalize kernel converts to FP64 and applies the scales, alpha and beta.
+//  * X3 (mixed precision): x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the
+//    products hi*hi + hi*lo + lo*hi accumulate in one FP32 accumulator.
+//
+// Tile: 128 x 64 outputs per CTA and one k-unit (OZ: <= 512; X3: all of k),
+// k-blocks of 32 BF16 (64-byte rows, 64-byte swizzle), every slice of A and B
+// for a k-block in one pipeline stage. Warp 0 issues TMA loads, warp 1 issues
+// tcgen05.mma, all four warps run the epilogue from TMEM. Every wait is bounded: on a timeout the kernel records an error,
+// drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bta_internal.cuh"
+#include "kernels_tc.cuh"
+#include "timing.cuh"
+
+namespace bta {
+namespace tc {
+
+constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int kUnitK = 512;     // k per unit in OZ mode (exactness bound of the d = 6 group)
+constexpr int kOzGroups = 6;    // d = 2..6 exact, d >= 7 shared
+constexpr int kFixShift = 49;   // int64 fixed point: value = T * 2^-49 * scales
+constexpr int kThreads = 128;
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls of try_wait (each suspends ~us) before giving up
+constexpr int kMaxStages = 4;
+
+__device__ int g_tc_error;  // set on a bounded-wait timeout
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// Bounded wait on an mbarrier phase; false (and the error word set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicExch(&g_tc_error, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 64 bytes, 64-byte
+// swizzle, 8-row groups 512 bytes apart (descriptor version 1).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused here)
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;                     // version
+  d |= (uint64_t)4 << 61;                     // swizzle 64B
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  int M, N;          // logical output size
+  int Kc;            // padded k extent of the slices (multiple of BK)
+  int unitk;         // k per work unit (multiple of BK)
+  int nunits;        // units per tile (grid = tiles x units x batch)
+  long long* T;      // OZ: [nb][Mpad][Npad] int64 accumulators (zeroed by the host)
+  int s;             // slices per operand
+  int mode;          // TC_OZ or TC_X3
+  int Mpad, Npad;    // padded rows of the A / B slice planes
+  int nstages;
+  int triA, triB;    // structure of op(A), op(B) (TRI_*), global k coordinates
+  int lowerC;
+  int nb;            // batch count
+  const double* sa;  // [nb][Mpad] row scales of A
+  const double* sb;  // [nb][Npad] column scales of B
+  double* C;
+  int64_t ldc, sC;
+  double alpha, beta;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // Work unit -> (batch z, tile (tm, tn), k-unit u).
+  const int tilesM = (g.M + BM - 1) / BM, tilesN = (g.N + BN - 1) / BN;
+  long long bid = blockIdx.x;
+  const int u = (int)(bid % g.nunits);
+  bid /= g.nunits;
+  const int tn = (int)(bid % tilesN);
+  bid /= tilesN;
+  const int tm = (int)(bid % tilesM);
+  const int z = (int)(bid / tilesM);
+  const int m0 = tm * BM, n0 = tn * BN;
+  if (g.lowerC && n0 > m0 + BM - 1) return;  // tile entirely above the diagonal
+
+  // k-block range of this unit (structural zeros of triangular operands skipped).
+  int kb, ke;
+  {
+    int gb = 0, ge = g.Kc;
+    if (g.triA == TRI_LOWER) ge = min(ge, m0 + BM);
+    if (g.triA == TRI_UPPER) gb = max(gb, m0);
+    if (g.triB == TRI_LOWER) gb = max(gb, n0);
+    if (g.triB == TRI_UPPER) ge = min(ge, n0 + BN);
+    gb = gb / BK * BK;
+    kb = max(gb, u * g.unitk);
+    ke = min(ge, (u + 1) * g.unitk);
+  }
+  const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+  if (nk == 0 && (g.mode == TC_OZ || u > 0)) return;  // nothing to add (X3 unit 0 still writes beta*C)
+
+  const int S = g.s;
+  const uint32_t a_bytes = BM * BK * 2, b_bytes = BN * BK * 2;
+  const uint32_t stage_bytes = (uint32_t)S * (a_bytes + b_bytes);
+  const int NS = g.nstages;
+
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int ngroups = g.mode == TC_OZ ? min(kOzGroups, S) : 1;
+
+  if (nk > 0) {
+    if (warp == 0 && lane == 0) {
+      // TMA producer.
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < nk && ok; ++it) {
+        const int st = it % NS;
+        if (it >= NS) ok = mbar_wait(&empty_bar[st], ((it / NS) - 1) & 1);
+        if (!ok) break;
+        mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
+        uint8_t* sbase = smem + (size_t)st * stage_bytes;
+        const int kx = kb + it * BK;
+        for (int p = 0; p < S; ++p)
+          tma_load_2d(sbase + p * a_bytes, &tmA, &full_bar[st], kx, (z * S + p) * g.Mpad + m0);
+        for (int q = 0; q < S; ++q)
+          tma_load_2d(sbase + S * a_bytes + q * b_bytes, &tmB, &full_bar[st], kx,
+                      (z * S + q) * g.Npad + n0);
+        ++issued;
+      }
+      if (!ok) {
+        // Drain the loads already in flight before leaving.
+        for (int it = max(0, issued - NS); it < issued; ++it) mbar_wait(&full_bar[it % NS], (it / NS) & 1);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // MMA issuer.
+      const uint32_t idesc = idesc_bf16_f32(BM, BN);  // 128 x 64
+      uint32_t started = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % NS;
+        if (!mbar_wait(&full_bar[st], (it / NS) & 1)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sbase = smem_u32(smem + (size_t)st * stage_bytes);
+        for (int p = 0; p < S; ++p) {
+          for (int q = 0; q < S; ++q) {
+            int grp;
+            if (g.mode == TC_OZ) {
+              if (p + q > S - 1) continue;  // (p+1) + (q+1) > S + 1
+              grp = min(p + q, kOzGroups - 1);
+            } else {
+              if (p + q > 1) continue;      // hi*hi, hi*lo, lo*hi
+              grp = 0;
+            }
+            const uint32_t a_addr = sbase + p * a_bytes;
+            const uint32_t b_addr = sbase + S * a_bytes + q * b_bytes;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t acc = (started >> grp) & 1u;
+              umma_bf16(tmem + grp * BN, sdesc_sw64(a_addr + kk * 32), sdesc_sw64(b_addr + kk * 32),
+                        idesc, acc);
+              started |= 1u << grp;
+            }
+          }
+        }
+        umma_commit(&empty_bar[st]);
+      }
+      umma_commit(&done_bar);
+    }
+    // Epilogue: every warp reads its 32 TMEM lanes (rows).
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int row = m0 + warp * 32 + lane;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      if (g.mode == TC_OZ) {
+        // Exact groups -> integers, all groups -> one int64 in units of 2^-49.
+        long long* Tz = g.T + ((int64_t)z * g.Mpad + row) * g.Npad;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t r[kOzGroups][16];
+#pragma unroll
+          for (int gi = 0; gi < kOzGroups; ++gi)
+            if (gi < ngroups) tmem_ld16(lane_base + gi * BN + c0, r[gi]);
+          tmem_wait_ld();
+          if (row < g.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              long long acc = 0;
+#pragma unroll
+              for (int gi = 0; gi < kOzGroups; ++gi) {
+                if (gi >= ngroups) break;
+                const float v = __uint_as_float(r[gi][j]);
+                // group gi holds sum d*d' 2^-7(gi+2); scale to units of 2^-49
+                // 2^(7(gi+2)) as an FP32 bit pattern: exact power-of-two scaling
+                if (gi < kOzGroups - 1) {
+                  const long long iv =
+                      __float2ll_rn(v * __int_as_float((127 + 7 * (gi + 2)) << 23));  // exact integer
+                  acc += iv << (kFixShift - 7 * (gi + 2));
+                } else {
+                  acc += __float2ll_rn(v * __int_as_float((127 + kFixShift) << 23));  // rounded to the quantum
+                }
+              }
+              if (acc) atomicAdd((unsigned long long*)(Tz + n0 + c0 + j), (unsigned long long)acc);
+            }
+          }
+        }
+      } else {
+        double* Cz = g.C + (int64_t)z * g.sC;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(lane_base + c0, r);
+          tmem_wait_ld();
+          if (row < g.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = n0 + c0 + j;
+              if (col >= g.N) break;
+              double* p = Cz + (int64_t)row * g.ldc + col;
+              double out = g.alpha * (double)__uint_as_float(r[j]);
+              if (g.beta != 0.0) out += g.beta * *p;
+              *p = out;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    // X3 with an empty k-range: C = beta * C on this tile.
+    const int row = m0 + warp * 32 + lane;
+    double* Cz = g.C + (int64_t)z * g.sC;
+    if (row < g.M)
+      for (int c = 0; c < BN && n0 + c < g.N; ++c) {
+        double* p = Cz + (int64_t)row * g.ldc + n0 + c;
+        *p = g.beta != 0.0 ? g.beta * *p : 0.0;
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Splitting kernels. The logical operand X is R x Kc (rows reduced over k):
+// element (r, k) of batch z is X[z*sz + r*sr + (k0 + k)*sk].
+// ---------------------------------------------------------------------------
+struct SplitArgs {
+  const double* X;
+  int64_t sr, sk, sz;
+  int R, Kc, k0, Kp;    // rows, k extent of the chunk, global k offset, padded k
+  int Rpad, s, mode, nb;
+  __nv_bfloat16* out;   // [nb][s][Rpad][Kp]
+  double* scale;        // [nb][Rpad]
+  unsigned long long* rowmax;  // [nb][Rpad] scratch (|x| bit patterns)
+};
+
+// Row maxima of |x| as FP64 bit patterns (order-preserving for non-negative values).
+__global__ void __launch_bounds__(256) split_rowmax_kernel(SplitArgs a) {
+  const int z = blockIdx.y;
+  const int r0 = blockIdx.x * 32;
+  const double* Xz = a.X + (int64_t)z * a.sz;
+  __shared__ unsigned long long red[8][32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  unsigned long long m = 0;
+  if (a.sk == 1) {
+    // rows contiguous in k: warp w takes rows r0 + w, w + 8, ...; lanes stride k
+    for (int rr = w; rr < 32; rr += 8) {
+      const int r = r0 + rr;
+      unsigned long long mr = 0;
+      if (r < a.R)
+        for (int k = lane; k < a.Kc; k += 32) {
+          const unsigned long long b =
+              (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + a.k0 + k]) & 0x7fffffffffffffffull;
+          mr = b > mr ? b : mr;
+        }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mr, off);
+        mr = o > mr ? o : mr;
+      }
+      if (lane == 0) red[0][rr] = mr;  // reuse: slot [0][row]
+    }
+    __syncthreads();
+    if (tid < 32 && r0 + tid < a.Rpad)
+      a.rowmax[(int64_t)z * a.Rpad + r0 + tid] = r0 + tid < a.R ? red[0][tid] : 0ull;
+  } else {
+    // rows contiguous across r: lane = row, warps split k
+    const int r = r0 + lane;
+    if (r < a.R)
+      for (int k = w; k < a.Kc; k += 8) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + (int64_t)(a.k0 + k) * a.sk]) &
+            0x7fffffffffffffffull;
+        m = b > m ? b : m;
+      }
+    red[w][lane] = m;
+    __syncthreads();
+    if (w == 0) {
+      for (int ww = 1; ww < 8; ++ww) m = red[ww][lane] > m ? red[ww][lane] : m;
+      if (r < a.Rpad) a.rowmax[(int64_t)z * a.Rpad + r] = r < a.R ? m : 0ull;
+    }
+  }
+}
+
+// Digit slices (OZ) or hi/lo slices (X3) of a 32 x 32 tile, plus row scales.
+__global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a) {
+  __shared__ double tile[32][33];
+  const int z = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const double* Xz = a.X + (int64_t)z * a.sz;
+  const int tid = threadIdx.x;
+  // Coalesced load along whichever dimension is contiguous.
+  for (int e = tid; e < 32 * 32; e += 256) {
+    int i, j;
+    if (a.sk == 1) { i = e / 32; j = e % 32; } else { j = e / 32; i = e % 32; }
+    const int r = r0 + i, k = c0 + j;
+    tile[i][j] = (r < a.R && k < a.Kc) ? Xz[(int64_t)r * a.sr + (int64_t)(a.k0 + k) * a.sk] : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < 32 * 32; e += 256) {
+    const int i = e / 32, j = e % 32;
+    const int r = r0 + i, k = c0 + j;
+    if (r >= a.Rpad || k >= a.Kp) continue;
+    const double x = tile[i][j];
+    __nv_bfloat16* o = a.out + (((int64_t)z * a.s) * a.Rpad + r) * a.Kp + k;
+    const int64_t plane = (int64_t)a.Rpad * a.Kp;
+    if (a.mode == TC_X3) {
+      const float xf = (float)x;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
+      o[0] = hi;
+      o[plane] = lo;
+      continue;
+    }
+    // Ozaki digits by integer arithmetic on the FP64 fields.
+    const unsigned long long mb = r < a.R ? a.rowmax[(int64_t)z * a.Rpad + r] : 0ull;
+    const int emax = (int)(mb >> 52);           // biased exponent of the row max
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    long long Y = 0;
+    if (emax > 0 && emax < 2047 && ex > 0) {
+      // |x| = M 2^(ex-1075); row scale 2^e with e = emax - 1021 puts |x| 2^-e below 1/2;
+      // Y = round(|x| 2^(7s - e)) = round(M 2^sh).
+      const long long M = (bits & 0x000fffffffffffffll) | 0x0010000000000000ll;
+      const int e = emax - 1021;
+      const int sh = ex - 1075 + 7 * a.s - e;
+      if (sh >= 0) Y = M << sh;                 // cannot overflow: Y < 2^(7s-1)
+      else if (sh > -64) Y = (M + (1ll << (-sh - 1))) >> (-sh);
+      if (bits < 0) Y = -Y;
+    }
+    // Balanced base-128 digits, least significant first: d_s ... d_2 in [-64, 63], d_1 the rest.
+    float dig[8];
+    for (int p = a.s - 1; p >= 1; --p) {
+      long long d = ((Y + 64) & 127) - 64;
+      dig[p] = (float)d;
+      Y = (Y - d) >> 7;
+    }
+    dig[0] = (float)Y;
+    float sc = 1.0f / 128.0f;
+    for (int p = 0; p < a.s; ++p) {
+      o[p * plane] = __float2bfloat16_rn(dig[p] * sc);  // exact: |d| <= 65, power-of-two scale
+      sc *= 1.0f / 128.0f;
+    }
+  }
+  if (a.mode == TC_OZ && blockIdx.x == 0 && tid < 32) {
+    const int r = r0 + tid;
+    if (r < a.Rpad) {
+      double sc = 0.0;
+      if (r < a.R) {
+        const unsigned long long mb = a.rowmax[(int64_t)z * a.Rpad + r];
+        const int emax = (int)(mb >> 52);
+        if (emax == 2047) sc = __longlong_as_double(0x7ff8000000000000ll);  // NaN/Inf row
+        else if (emax > 0) sc = ldexp(1.0, emax - 1021);
+        else sc = 1.0;  // zero (or subnormal-only) row: digits are zero
+      }
+      a.scale[(int64_t)z * a.Rpad + r] = sc;
+    }
+  }
+  if (a.mode == TC_X3 && blockIdx.x == 0 && tid < 32 && r0 + tid < a.Rpad)
+    a.scale[(int64_t)z * a.Rpad + r0 + tid] = 1.0;
+}
+
+// C = alpha * T 2^-49 sa_i sb_j + beta * C on the elements the GEMM computed.
+__global__ void __launch_bounds__(256) tc_finalize_kernel(const long long* T, int M, int N, int Mpad,
+                                                          int Npad, const double* sa,
+                                                          const double* sb, double* C, int64_t ldc,
+                                                          int64_t sC, double alpha, double beta,
+                                                          int lowerC) {
+  const int z = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * N) return;
+  const int i = (int)(e / N), j = (int)(e % N);
+  if (lowerC && (j / BN) * BN > (i / BM) * BM + BM - 1) return;
+  const double v = (double)T[((int64_t)z * Mpad + i) * Npad + j];
+  const double q = 1.0 / (double)(1ll << kFixShift);  // 2^-49, exact
+  double out = (v * q) * (alpha * sa[(int64_t)z * Mpad + i]) * sb[(int64_t)z * Npad + j];
+  double* p = C + (int64_t)z * sC + (int64_t)i * ldc + j;
+  if (beta != 0.0) out += beta * *p;
+  *p = out;
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+using namespace tc;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t kp, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {kp, rows};
+  const cuuint64_t strides[1] = {kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static inline int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int tc_slices(int mode) { return mode == TC_X3 ? 2 : kOzSlices; }
+
+// Bytes of scratch one chunk of `nb` batch entries needs (k extent K).
+static size_t tc_chunk_bytes(int mode, int M, int N, int K, int nb) {
+  const int64_t s = tc_slices(mode);
+  const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, BK);
+  size_t b = 0;
+  b += rup((Mp + Np) * Kp * s * 2 * nb, 256);  // slices
+  b += rup((Mp + Np) * 8 * nb, 256);           // scales
+  b += rup((Mp + Np) * 8 * nb, 256);           // row maxima
+  if (mode == TC_OZ) b += rup(Mp * Np * 8 * nb, 256);  // int64 accumulators
+  return b;
+}
+
+static int tc_batch_chunk(int M, int N, int K) {
+  // Keep one chunk's slice planes and accumulators near 512 MB.
+  const int64_t per = (rup(M, BM) + rup(N, BN)) * rup(K, BK) * kOzSlices * 2 + rup(M, BM) * rup(N, BN) * 8;
+  int64_t nb = (512ll << 20) / (per > 0 ? per : 1);
+  return (int)(nb < 1 ? 1 : (nb > 64 ? 64 : nb));
+}
+
+size_t tc_workspace_bytes(int mode, int M, int N, int K, int batch) {
+  const int c = tc_batch_chunk(M, N, K);
+  return tc_chunk_bytes(mode, M, N, K, batch < c ? batch : c);
+}
+
+static cudaError_t split_operand(const double* X, int64_t sr, int64_t sk, int64_t sz, int R, int Kc,
+                                 int Kp, int Rpad, int s, int mode, int nb, __nv_bfloat16* out,
+                                 double* scale, unsigned long long* rowmax, cudaStream_t st) {
+  SplitArgs a{};
+  a.X = X; a.sr = sr; a.sk = sk; a.sz = sz; a.R = R; a.Kc = Kc; a.k0 = 0; a.Kp = Kp;
+  a.Rpad = Rpad; a.s = s; a.mode = mode; a.nb = nb; a.out = out; a.scale = scale; a.rowmax = rowmax;
+  if (mode == TC_OZ) split_rowmax_kernel<<<dim3((Rpad + 31) / 32, nb), 256, 0, st>>>(a);
+  split_digits_kernel<<<dim3((Kp + 31) / 32, (Rpad + 31) / 32, nb), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+static int g_smem_attr_set = 0;
+
+cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (g.nterms != 1) return cudaErrorInvalidValue;
+  const GemmTerm& t = g.t[0];
+  const int S = tc_slices(mode);
+  const int M = g.M, N = g.N, K = t.K;
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if (K > 16384) return cudaErrorInvalidValue;  // int64 accumulator headroom
+  const int Mp = (int)rup(M, BM), Np = (int)rup(N, BN), Kp = (int)rup(K, BK);
+  const int total = g.nb1 * g.nb2;
+  // Batch entries per pass: as many as the design size and the workspace allow.
+  int chunk_nb = tc_batch_chunk(M, N, K);
+  if (chunk_nb > total) chunk_nb = total;
+  while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, K, chunk_nb) > ws_bytes) --chunk_nb;
+  if (tc_chunk_bytes(mode, M, N, K, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
+  // Dynamic shared memory: the opt-in limit less the kernel's static shared memory.
+  static size_t dyn_limit = 0;
+  if (!dyn_limit) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, tc_gemm_kernel);
+    if (e != cudaSuccess) return e;
+    dyn_limit = (size_t)optin - fa.sharedSizeBytes;
+  }
+  const uint32_t stage_bytes = (uint32_t)S * (BM + BN) * BK * 2;
+  int nstages = (int)((dyn_limit - 1024) / stage_bytes);
+  if (nstages > kMaxStages) nstages = kMaxStages;
+  if (nstages < 1) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)nstages * stage_bytes + 1024;
+  if ((size_t)g_smem_attr_set < smem) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    g_smem_attr_set = (int)smem;
+  }
+
+  // Operand strides: op(A) element (m, k); op(B)^T element (n, k).
+  const int64_t a_sr = t.opA == OP_N ? t.lda : 1, a_sk = t.opA == OP_N ? 1 : t.lda;
+  const int64_t b_sr = t.opB == OP_N ? 1 : t.ldb, b_sk = t.opB == OP_N ? t.ldb : 1;
+  const int unitk = mode == TC_OZ ? kUnitK : Kp;
+  const int nunits = (Kp + unitk - 1) / unitk;
+  // Batch index: one stride dimension (callers use nb2 == 1, or nb1 == 1).
+  const int64_t bsA = g.nb2 == 1 ? t.sA1 : t.sA2, bsB = g.nb2 == 1 ? t.sB1 : t.sB2;
+  const int64_t bsC = g.nb2 == 1 ? g.sC1 : g.sC2;
+
+  for (int c0 = 0; c0 < total; c0 += chunk_nb) {
+    const int nb = total - c0 < chunk_nb ? total - c0 : chunk_nb;
+    char* w = (char*)ws;
+    __nv_bfloat16* As = (__nv_bfloat16*)w;
+    __nv_bfloat16* Bs = As + (int64_t)nb * S * Mp * Kp;
+    w += rup(((int64_t)Mp + Np) * Kp * S * 2 * nb, 256);
+    double* sa = (double*)w;
+    double* sb = sa + (int64_t)nb * Mp;
+    w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
+    unsigned long long* rmA = (unsigned long long*)w;
+    unsigned long long* rmB = rmA + (int64_t)nb * Mp;
+    w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
+    long long* Tacc = (long long*)w;
+    const double* A0 = t.A + (int64_t)c0 * bsA;
+    const double* B0 = t.B + (int64_t)c0 * bsB;
+    double* C0 = g.C + (int64_t)c0 * bsC;
+    cudaError_t e = split_operand(A0, a_sr, a_sk, bsA, M, K, Kp, Mp, S, mode, nb, As, sa, rmA, s);
+    if (e != cudaSuccess) return e;
+    e = split_operand(B0, b_sr, b_sk, bsB, N, K, Kp, Np, S, mode, nb, Bs, sb, rmB, s);
+    if (e != cudaSuccess) return e;
+    if (mode == TC_OZ) {
+      e = cudaMemsetAsync(Tacc, 0, (size_t)nb * Mp * Np * 8, s);
+      if (e != cudaSuccess) return e;
+    }
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, As, (uint64_t)nb * S * Mp, (uint64_t)Kp, BM) ||
+        !make_map(&mB, Bs, (uint64_t)nb * S * Np, (uint64_t)Kp, BN))
+      return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.T = Tacc;
+    a.s = S; a.mode = mode; a.Mpad = Mp; a.Npad = Np;
+    a.nstages = nstages; a.triA = t.triA; a.triB = t.triB; a.lowerC = g.lowerC; a.nb = nb;
+    a.sa = sa; a.sb = sb;
+    a.C = C0; a.ldc = g.ldc; a.sC = bsC;
+    a.alpha = t.alpha; a.beta = g.beta;
+    const long long grid = (long long)(Mp / BM) * (Np / BN) * nunits * nb;
+    {
+      TimedLaunch tl(K_GEMM_TC, 2.0 * M * N * (double)K * nb * (g.lowerC && M == N ? 0.5 : 1.0), s);
+      tc_gemm_kernel<<<(unsigned)grid, kThreads, smem, s>>>(mA, mB, a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    if (mode == TC_OZ) {
+      const int64_t elems = (int64_t)M * N;
+      tc_finalize_kernel<<<dim3((unsigned)((elems + 255) / 256), nb), 256, 0, s>>>(
+          Tacc, M, N, Mp, Np, sa, sb, C0, g.ldc, bsC, t.alpha, g.beta, g.lowerC);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_error_read_reset(int* out) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
+  if (e != cudaSuccess) return e;
+  *out = v;
+  const int zero = 0;
+  return cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+}
+
+}  // namespace bta

@@ -20,6 +20,7 @@ enum KernelId {
   K_GEMV,
   K_ARROW,
   K_PROBE,
+  K_GEMM_TC,
   K_COUNT
 };
 
