@@ -38,8 +38,11 @@ WORKLOADS = {
     "n365_b1024_a8": dict(n=365, b=1024, a=8, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
     "n16_b32_a4": dict(n=16, b=32, a=4, shift=gen.SHIFT_PLUS_ONE, shift_name="1 + row sum"),
     "n256_b2048_a16": dict(n=256, b=2048, a=16, shift=gen.SHIFT_1_001, shift_name="1.001 x row sum"),
+    # small case with the same block shapes, for profiler captures (a few GB on the device)
+    "n48_b1024_a8": dict(n=48, b=1024, a=8, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
 }
 NRHS = 4
+BATCH_WORKLOAD = "batch64_n20-200_b128-512_a2-8"
 
 
 # Algorithmic FP64 flops (LAPACK counts of the method itself).
@@ -53,6 +56,26 @@ def flops_selinv(n, b, a):
 
 def flops_solve(n, b, a, r):
     return 2 * r * (n * b * b + 2 * (n - 1) * b * b + 2 * n * a * b + a * a)
+
+
+KERNELS = ["gemm_f64", "potrf_panel", "trsm_panel", "tile_inv", "zero_upper", "mirror", "logdet", "trsv",
+           "gemv", "arrow", "probe", "gemm_tc", "tc_split", "tc_final"]
+# tensor-core products per FP64 product in each precision mode
+TC_PAIRS = {"ozaki": 28, "bf16x3": 3}
+PREC_DTYPE = {"fp64": "f64", "ozaki": "bf16 slices x7 (FP64-emulated, Ozaki splitting)",
+              "bf16x3": "bf16x3 (FP32 accumulation) + f64"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_burst": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "source": "MEASURED_PEAKS.json (measured)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_burst": 1900.0, "bf16_sustained": 1700.0, "hbm_gbs": 6800.0,
+                "source": "profiling-recipe fallback"}
 
 
 def pattern_bytes(n, b, a):
@@ -188,12 +211,207 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def make_batch(count=64, seed=2026):
+    """64 seeded matrices: n ~ U[20, 200], b in {128, 256, 512}, a in {2, 4, 8},
+    generator seed base + k (the batched workload)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(20, 201))
+        b = int(rng.choice([128, 256, 512]))
+        a = int(rng.choice([2, 4, 8]))
+        out.append(gen.make_bta(n, b, a, seed=seed + k, shift=gen.SHIFT_1_01))
+    return out
+
+
+def run_batch(args):
+    """Batched form: 64 sequential plain FP64 calls vs. one tuned batched call
+    replayed from a CUDA graph (the reset copy of the inputs is in both)."""
+    import torch
+    import paper_2503_17528_gb300 as bta
+    from paper_2503_17528_gb300 import tune
+    from paper_2503_17528_gb300.batched import Batch
+    dev = torch.device("cuda", 0)
+    raw = make_batch()
+    P = [tuple(torch.from_numpy(x).to(dev) for x in m) for m in raw]
+    W = [tuple(x.clone() for x in m) for m in P]
+    flops = sum(flops_factor(m[0].shape[0], m[0].shape[1], m[3].shape[0]) +
+                flops_selinv(m[0].shape[0], m[0].shape[1], m[3].shape[0]) for m in raw)
+
+    def reset():
+        for w, p in zip(W, P):
+            for x, y in zip(w, p):
+                if x.numel():
+                    x.copy_(y, non_blocking=True)
+
+    bta.set_precision("fp64")
+    lds = torch.empty(len(W), dtype=torch.float64, device=dev)
+
+    def sequential():
+        reset()
+        for k, (d, l, ar, t) in enumerate(W):
+            bta.factor(d, l, ar, t)
+            bta.logdet(d, t, out=lds[k])
+            bta.selinv(d, l, ar, t)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    seq_ms = timed(sequential, args.steps)
+    seq_out = [tuple(x.clone() for x in w) for w in W]
+    cfg = tune.lookup(W)
+    tuned_now = cfg is None
+    if cfg is None:
+        cfg = tune.tune(W, P)
+    batch = Batch(W, policy=cfg["policy"], nstreams=cfg["nstreams"])
+    reset()
+    batch.run()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        graph = batch.capture()
+    torch.cuda.current_stream().wait_stream(side)
+
+    def replay():
+        reset()
+        graph.replay()
+
+    graph_ms = timed(replay, args.steps)
+    worst = 0.0
+    for w, r in zip(W, seq_out):
+        for x, y in zip(w, r):
+            if y.numel():
+                num = torch.linalg.norm((x - y).flatten(1) if x.dim() == 3 else (x - y).flatten(0)[None], dim=1)
+                den = torch.linalg.norm(y.flatten(1) if y.dim() == 3 else y.flatten(0)[None], dim=1)
+                worst = max(worst, float((num / den.clamp_min(1e-300)).max()))
+    line = {"metric": "BTA batched factor+logdet+selinv ms/batch (64 uneven matrices)",
+            "value": round(graph_ms, 3), "unit": "ms/batch", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(graph_ms, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if cfg["policy"] == "fp64" else
+            "f64 + bf16-slice FP64 emulation (b >= 256)" if cfg["policy"] == "ozaki_b256" else "bf16 slices (FP64-emulated)",
+            "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "matrices": len(raw), "total_flops": flops,
+                       "steps_include": "device reset copy + all 64 matrices"},
+            "sequential_plain_fp64_ms": round(seq_ms, 3), "speedup_vs_sequential": round(seq_ms / graph_ms, 3),
+            "tflops_per_gpu": round(flops / (graph_ms * 1e-3) / 1e12, 4),
+            "tuned": {k: cfg[k] for k in ("nstreams", "policy", "ms")}, "tuned_in_this_run": tuned_now,
+            "tuning_table": cfg.get("table"),
+            "max_block_rel_err_vs_sequential_fp64": float(f"{worst:.3e}")}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def workload_config(w):
     n, b, a = w["n"], w["b"], w["a"]
     return {"workload": f"n{n}_b{b}_a{a}", "n": n, "b": b, "a": a, "nrhs": NRHS,
             "dominance_shift": w["shift_name"], "generator": "seeded N(0,1)/sqrt(b) blocks, diagonally dominant",
             "l2": f"inputs {pattern_bytes(n, b, a) / 1e9:.2f} GB per matrix > 129 MB L2; no flush",
             "steps_include": "device reset copy + factor + logdet + solve + selinv"}
+
+
+def read_kernel_stats(lib):
+    stats = {}
+    for kid, name in enumerate(KERNELS):
+        tms, fl, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        lib.bta_timing_read(kid, ctypes.byref(tms), ctypes.byref(fl), ctypes.byref(cnt))
+        if cnt.value:
+            stats[name] = (tms.value, fl.value, cnt.value)
+    return stats
+
+
+def roofline_of(stats, prec, fp64_peak, peaks):
+    """Roofline of the dominant kernel of one step (largest summed device time)."""
+    top = max(stats.items(), key=lambda kv: kv[1][0])
+    name, (ms, fl, cnt) = top
+    total = sum(v[0] for v in stats.values())
+    base = {"kernel": name, "kernel_share_of_step": round(ms / total, 4) if total else None,
+            "avg_launch_ms": round(ms / max(cnt, 1), 5), "launches_per_step": int(cnt), "traffic": None}
+    if name == "gemm_tc":
+        pairs = TC_PAIRS.get(prec, 1)
+        ach = pairs * fl / (ms * 1e-3) / 1e12
+        base.update({"bound": "tensor", "achieved": round(ach, 3), "peak": peaks["bf16_sustained"],
+                     "unit": "TFLOP/s", "frac": round(ach / peaks["bf16_sustained"], 4),
+                     "peak_source": peaks["source"] + ", bf16 sustained",
+                     "fp64_equivalent_tflops": round(fl / (ms * 1e-3) / 1e12, 3),
+                     "achieved_counts": f"{pairs} BF16 slice products per FP64 product"})
+    else:
+        ach = fl / (ms * 1e-3) / 1e12 if ms > 0 and fl > 0 else None
+        base.update({"bound": "alu", "achieved": round(ach, 4) if ach else None, "peak": round(fp64_peak, 4),
+                     "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4) if ach else None,
+                     "peak_source": "measured live: bta_probe_fp64_peak DMMA loop on all SMs"})
+    return base
+
+
+def run_modes(args, bta, lib, step, W, ld_out, base_ms, dev, ref_inputs):
+    """Time the other precision modes on the same matrix; state each one's error
+    against the main mode's result (per block, relative Frobenius) and its speedup."""
+    import torch
+    ref = [x.clone() for x in W]
+    ref_ld = float(ld_out.item())
+    res = {}
+    for mode in [m for m in args.modes.split(",") if m and m != args.precision]:
+        bta.set_precision(mode)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+
+        def blockerr(x, y):
+            if x.numel() == 0:
+                return 0.0
+            if x.dim() == 3:
+                num = torch.linalg.norm((x - y).flatten(1), dim=1)
+                den = torch.linalg.norm(y.flatten(1), dim=1).clamp_min(1e-300)
+                return float((num / den).max())
+            return float(torch.linalg.norm(x - y) / torch.linalg.norm(y).clamp_min(1e-300))
+
+        errs = {nm: blockerr(W[i], ref[i]) for i, nm in enumerate(["X_diag", "X_lower", "X_arrow", "X_tip"])}
+        errs["solve"] = blockerr(W[4], ref[4])
+        errs["logdet"] = abs(float(ld_out.item()) - ref_ld) / abs(ref_ld)
+        # phase split of one step in this mode
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for dst, src in zip(W, ref_inputs):
+            dst.copy_(src)
+        D, Lo, Ar, Ti, R = W
+        evs[0].record()
+        bta.factor(D, Lo, Ar, Ti)
+        evs[1].record()
+        bta.solve(D, Lo, Ar, Ti, R)
+        evs[2].record()
+        bta.selinv(D, Lo, Ar, Ti)
+        evs[3].record()
+        torch.cuda.synchronize(dev)
+        phases = {nm: round(evs[i].elapsed_time(evs[i + 1]), 3) for i, nm in enumerate(["factor", "solve", "selinv"])}
+        lib.bta_timing_enable(1)
+        step()
+        torch.cuda.synchronize(dev)
+        stats = read_kernel_stats(lib)
+        lib.bta_timing_enable(0)
+        peaks = measured_peaks()
+        res[mode] = {"phase_ms": phases,"ms_per_matrix": round(ms, 3), "speedup_vs_" + args.precision: round(base_ms / ms, 3),
+                     "max_block_rel_err_vs_" + args.precision: {k: float(f"{v:.3e}") for k, v in errs.items()},
+                     "dtype": PREC_DTYPE[mode],
+                     "roofline": roofline_of(stats, mode, 1.0, peaks),
+                     "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()}}
+    return res
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -208,6 +426,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.set_device(dev)
     lib = _lib.load()
     n, b, a = w["n"], w["b"], w["a"]
+    bta.set_precision(args.precision)
 
     arrays = make_workload(w, seed=rank)
     d, l, ar, t, r = arrays
@@ -298,6 +517,10 @@ def run_ours(args, w, rank, world, local_rank):
         del H, O
 
     F = flops_factor(n, b, a) + flops_selinv(n, b, a)
+    modes = {}
+    if rank == 0 and args.modes:
+        modes = run_modes(args, bta, lib, step, W, ld_out, ms_per_step, dev, P)
+        bta.set_precision(args.precision)
     out = None
     if rank == 0:
         # Kernel-level measurement pass (after the timed steps): per-launch events
@@ -323,13 +546,9 @@ def run_ours(args, w, rank, world, local_rank):
         lib.bta_timing_enable(1)
         step()
         torch.cuda.synchronize(dev)
-        stats = {}
-        for kid, name in enumerate(["gemm_f64", "potrf_tile", "trsm_panel", "tile_inv", "zero_upper",
-                                    "mirror", "logdet", "trsv", "gemv", "arrow"]):
-            tms, fl, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-            lib.bta_timing_read(kid, ctypes.byref(tms), ctypes.byref(fl), ctypes.byref(cnt))
-            stats[name] = (tms.value, fl.value, cnt.value)
+        stats = read_kernel_stats(lib)
         lib.bta_timing_enable(0)
+        peaks = measured_peaks()
         probe_out = torch.zeros(1, dtype=torch.float64, device=dev)
         pf = ctypes.c_double()
         lib.bta_probe_fp64_peak(ctypes.c_void_p(probe_out.data_ptr()), 200, ctypes.byref(pf),
@@ -342,31 +561,24 @@ def run_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         peak_tf = pf.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
-        g_ms, g_fl, g_cnt = stats["gemm_f64"]
         total_kernel_ms = sum(v[0] for v in stats.values())
         launches_per_step = sum(v[2] for v in stats.values())
-        achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
-        tflops = F / (ms_per_step * 1e-3 / 1.0) / 1e12 * 1.0
+        tflops = F / (ms_per_step * 1e-3) / 1e12
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": "ms/matrix", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": PREC_DTYPE[args.precision], "precision_mode": args.precision,
             "data": "synthetic", "config": workload_config(w),
-            "tflops_per_gpu": round(F / (ms_per_step * 1e-3) / 1e12, 4),
+            "tflops_per_gpu": round(tflops, 4),
             "fp64_peak_tflops_measured": round(peak_tf, 4),
             "frac_of_fp64_peak": round(tflops / peak_tf, 4),
-            "roofline": {
-                "bound": "alu", "achieved": round(achieved, 4) if achieved else None,
-                "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tf, 4) if achieved else None, "traffic": None,
-                "kernel": "gemm_f64_kernel (DMMA m8n8k4)",
-                "peak_source": "measured live: bta_probe_fp64_peak DMMA loop on all SMs",
-                "kernel_share_of_step": round(g_ms / total_kernel_ms, 4) if total_kernel_ms else None,
-                "avg_launch_ms": round(g_ms / max(g_cnt, 1), 5),
-            },
+            "roofline": roofline_of(stats, args.precision, peak_tf, peaks),
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()},
+            "kernel_total_ms_per_step": round(total_kernel_ms, 3),
             "phase_ms": phases,
             "gpu_launches": int(launches_per_step * args.steps),
+            "modes": modes or None,
             "e2e": e2e,
         }
         if clocks:
@@ -387,10 +599,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n365_b1024_a8")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="n365_b1024_a8")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
+    ap.add_argument("--precision", choices=["fp64", "ozaki", "bf16x3"], default="fp64")
+    ap.add_argument("--modes", default="ozaki,bf16x3",
+                    help="other precision modes timed on the same matrix ('' to skip)")
     ap.add_argument("--cpu-target-s", type=float, default=10.0)
     ap.add_argument("--ref-target-s", type=float, default=5.0)
     args = ap.parse_args()
@@ -398,6 +613,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == BATCH_WORKLOAD:
+        return run_batch(args) if args.impl == "ours" else 0
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, rank, world)

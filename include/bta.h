@@ -153,6 +153,66 @@ int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag,
 int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double* diag,
                        const double* tip, double* out_dev, bta_stream_t stream);
 
+/* ---- Batched form -------------------------------------------------------- */
+
+/* One matrix of a batch: its blocks (in place: A -> X), an optional device
+ * double for its log-determinant, its precision mode and a workspace of at
+ * least bta_batch_workspace_bytes(n, b, a, prec) bytes (256-byte aligned). */
+typedef struct bta_batch_entry {
+  int64_t n, b, a;
+  double* diag;
+  double* lower;
+  double* arrow;
+  double* tip;
+  double* logdet_out;
+  int prec;
+  void* ws;
+  size_t ws_bytes;
+} bta_batch_entry;
+
+size_t bta_batch_workspace_bytes(int64_t n, int64_t b, int64_t a, int prec);
+
+/*
+ * bta_factor_selinv_batched -- factor, log-det and selected inversion of
+ * `count` independent BTA matrices of any sizes (not in the paper; a batch of
+ * the Algorithm 1 + Algorithm 2 pipeline). Matrices are taken largest first and
+ * each goes to whichever of `nstreams` (1..64) library streams has the least work
+ * so far; the streams fork from `stream` and join back into it, so the whole
+ * batch is ordered on `stream` and can be captured in one CUDA graph (capture
+ * `stream`; the library's streams join the capture through events). Returns -2
+ * if any entry is invalid (nothing enqueued). A failed pivot in any matrix sets
+ * the shared info word (which matrix is not recorded).
+ */
+int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int nstreams,
+                              bta_stream_t stream);
+
+/* ---- Differentiation support ------------------------------------------- */
+
+/*
+ * bta_grad_blocks -- gradients of  f = alpha * log det A + beta * x^T A^{-1} x
+ * with respect to the stored blocks and to x, given the selected inverse X
+ * (bta_selinv output) and y = A^{-1} x (bta_solve output):
+ *   df/d diag_i  = alpha X_ii      - beta y_i y_i^T
+ *   df/d lower_i = 2 (alpha X_{i+1,i} - beta y_{i+1} y_i^T)
+ *   df/d arrow_i = 2 (alpha X_{n,i}   - beta y_n y_i^T)
+ *   df/d tip     = alpha X_nn      - beta y_n y_n^T
+ *   df/dx        = 2 beta y                    (g_x may be NULL)
+ * since d log det A / dA = A^{-1} and d x^T A^{-1} x / dA = -y y^T; each
+ * off-diagonal block stands for itself and its transpose (factor 2) and the
+ * diagonal blocks take the symmetric convention. Not in the paper: it is what
+ * makes the selected inverse the backward of a Gaussian log-likelihood.
+ * y, g_x: [N] device vectors; outputs have the layout of the inputs.
+ */
+int bta_grad_blocks(int64_t n, int64_t b, int64_t a, const double* x_diag, const double* x_lower,
+                    const double* x_arrow, const double* x_tip, const double* y, double alpha,
+                    double beta, double* g_diag, double* g_lower, double* g_arrow, double* g_tip,
+                    double* g_x, bta_stream_t stream);
+
+/* bta_dot -- out_dev = x^T y over N doubles, summed in a fixed order (identical
+ * bits on repeat); ws: >= 608 doubles of device scratch. */
+int bta_dot(int64_t N, const double* x, const double* y, double* out_dev, void* ws,
+            size_t ws_bytes, bta_stream_t stream);
+
 /* ---- Precision of the block products ------------------------------------ */
 
 #define BTA_PREC_FP64 0   /* FP64 DMMA (mma.sync f64) everywhere (default) */
@@ -210,7 +270,11 @@ int bta_tc_status(int* timed_out);
 #define BTA_KERNEL_GEMV 8
 #define BTA_KERNEL_ARROW 9
 #define BTA_KERNEL_PROBE 10
-#define BTA_KERNEL_GEMM_TC 11  /* tcgen05 BF16-slice GEMM (OZAKI / BF16X3 modes) */
+#define BTA_KERNEL_GEMM_TC 11  /* tcgen05 BF16-slice GEMM (OZAKI / BF16X3 modes); flops recorded
+                                  as the FP64 product it stands for (2 M N K, lower half for
+                                  lower-only outputs) */
+#define BTA_KERNEL_TC_SPLIT 12 /* FP64 -> BF16 slice splitting */
+#define BTA_KERNEL_TC_FINAL 13 /* int64 accumulator -> FP64 output */
 
 /*
  * bta_timing_enable -- on != 0: from now on every kernel launch of the library

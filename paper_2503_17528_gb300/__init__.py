@@ -28,3 +28,4 @@ from .api import (  # noqa: F401
     tc_status,
     workspace_bytes,
 )
+from .autograd import BTALogdetQuad, logdet_quad  # noqa: F401,E402

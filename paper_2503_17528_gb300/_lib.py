@@ -32,6 +32,11 @@ _SIGS = {
     "bta_timing_read": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(_i64)],
     "bta_probe_fp64_peak": [_p, _i64, ctypes.POINTER(ctypes.c_double), _p],
+    "bta_batch_workspace_bytes": [_i64, _i64, _i64, ctypes.c_int],
+    "bta_factor_selinv_batched": [_i64, ctypes.c_void_p, ctypes.c_int, _p],
+    "bta_grad_blocks": [_i64, _i64, _i64, _p, _p, _p, _p, _p, ctypes.c_double, ctypes.c_double,
+                        _p, _p, _p, _p, _p, _p],
+    "bta_dot": [_i64, _p, _p, _p, _p, _sz, _p],
     "bta_set_precision": [ctypes.c_int],
     "bta_get_precision": [],
     "bta_gemm_workspace_bytes": [ctypes.c_int, _i64, _i64, _i64],
@@ -40,6 +45,11 @@ _SIGS = {
     "bta_tc_status": [ctypes.POINTER(ctypes.c_int)],
     "bta_version": [],
 }
+
+class BatchEntry(ctypes.Structure):
+    _fields_ = [("n", _i64), ("b", _i64), ("a", _i64), ("diag", _p), ("lower", _p), ("arrow", _p),
+                ("tip", _p), ("logdet_out", _p), ("prec", ctypes.c_int), ("ws", _p), ("ws_bytes", _sz)]
+
 
 _lib = None
 

@@ -3,6 +3,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "../../include/bta.h"
 #include "bta_internal.cuh"
 #include "kernels_tc.cuh"
@@ -37,31 +41,31 @@ struct FactorWs { double *Linv, *W, *Wa; void* tc; size_t tc_bytes; };
 struct SelinvWs { double *Linv, *G, *H, *LtInv; void* tc; size_t tc_bytes; };
 
 extern int g_prec;
-size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch);
+size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch, int prec);
 struct SolveWs { double* partial; };
 struct LogdetWs { double* partial; };
 
-size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o) {
+size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o, int prec) {
   (void)n;
   Carver c(p);
   FactorWs w;
   w.Linv = c.take((size_t)(b * b));
   w.W = c.take((size_t)(b * b));
   w.Wa = c.take((size_t)(a * b + 1));
-  w.tc_bytes = tc_bytes_for(b, a, 1);
+  w.tc_bytes = tc_bytes_for(b, a, 1, prec);
   w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
   if (o) *o = w;
   return c.off;
 }
 
-size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o) {
+size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o, int prec) {
   Carver c(p);
   SelinvWs w;
   w.Linv = c.take((size_t)(n * b * b));
   w.G = c.take((size_t)((n - 1) * b * b + 1));
   w.H = c.take((size_t)(n * a * b + 1));
   w.LtInv = c.take((size_t)(a * a + 1));
-  w.tc_bytes = tc_bytes_for(b, a, n);
+  w.tc_bytes = tc_bytes_for(b, a, n, prec);
   w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
   if (o) *o = w;
   return c.off;
@@ -131,33 +135,34 @@ bool routes_to_tc(int prec, int cls) {
   return false;
 }
 
-bool tc_eligible(const GemmTerm& t, int M, int N) { return M >= 64 && N >= 64 && t.K >= 64; }
 
 struct TcWs {
   void* p = nullptr;
   size_t bytes = 0;
 };
 
-// Runs a (one- or two-term) GEMM: eligible terms on the tensor cores in the
-// current precision mode, the rest with the FP64 DMMA kernel (later terms
-// accumulate with beta = 1).
-cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, cudaStream_t s) {
-  const int prec = g_prec;
+// Runs a (one- or two-term) GEMM. In a tensor-core precision mode an eligible
+// product goes to gemm_tc (two terms concatenated along k there); otherwise the
+// FP64 DMMA kernels run it.
+cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaStream_t s) {
   if (prec == BTA_PREC_FP64 || !routes_to_tc(prec, cls) || !tw.p) return gemm_f64(g, s);
-  for (int i = 0; i < g.nterms; ++i) {
-    GemmArgs gi = g;
-    gi.t[0] = g.t[i];
-    gi.nterms = 1;
-    if (i > 0) gi.beta = 1.0;
-    cudaError_t e = tc_eligible(gi.t[0], g.M, g.N) ? gemm_tc(gi, tc_mode_of(prec), tw.p, tw.bytes, s)
-                                                  : gemm_f64(gi, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  int kmax = 0;
+  for (int i = 0; i < g.nterms; ++i) kmax = g.t[i].K > kmax ? g.t[i].K : kmax;
+  if (g.M >= 64 && g.N >= 64 && kmax >= 64) return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s);
+  return gemm_f64(g, s);
+}
+
+// TRTRI's doubling products, routed like the TRSM substitution they serve.
+struct HookCtx {
+  TcWs tw;
+  int prec;
+};
+cudaError_t trtri_hook(const GemmArgs& g, void* ctx, cudaStream_t s) {
+  return gemm_run(g, CLS_TRSM, ((HookCtx*)ctx)->tw, ((HookCtx*)ctx)->prec, s);
 }
 
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
-                double* tip, const FactorWs& w, cudaStream_t s) {
+                double* tip, const FactorWs& w, int prec, cudaStream_t s) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b;
   TcWs tw;
@@ -166,32 +171,33 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
     BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
-    BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s));
+    HookCtx hc{tw, prec};
+    BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
     if (i + 1 < n) {
       double* Li = lower + i * bb;
       // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
       BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.W, b, B, B, 0.0, 0), CLS_TRSM, tw, s));
+                                w.W, b, B, B, 0.0, 0), CLS_TRSM, tw, prec, s));
       BTA_TRY(cudaMemcpyAsync(Li, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
       // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
       BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
-                                Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, s));
+                                Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s));
     }
     if (a > 0) {
       double* Ai = arrow + i * a * b;
       // L_{n,i} = A_{n,i} L_ii^{-T}
       BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.Wa, b, Aa, B, 0.0, 0), CLS_TRSM, tw, s));
+                                w.Wa, b, Aa, B, 0.0, 0), CLS_TRSM, tw, prec, s));
       BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
       if (i + 1 < n) {
         // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
         BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, lower + i * bb, b, OP_T, TRI_NONE,
                                        B, -1.0),
-                                  Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, s));
+                                  Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
       }
       // A_{n,n} -= L_{n,i} L_{n,i}^T
       BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
-                                tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, s));
+                                tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, prec, s));
     }
   }
   if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
@@ -199,37 +205,38 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
 }
 
 int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
-                double* tip, const SelinvWs& w, cudaStream_t s) {
+                double* tip, const SelinvWs& w, int prec, cudaStream_t s) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b, ab = a * b;
   TcWs tw;
   tw.p = w.tc;
   tw.bytes = w.tc_bytes;
   // Prologue, independent over i: L_ii^{-1}, G_i, H_i, M_i; then X_nn.
-  BTA_TRY(trtri_blocks(diag, b, bb, w.Linv, b, bb, (int)n, B, s));
+  HookCtx hc{tw, prec};
+  BTA_TRY(trtri_blocks(diag, b, bb, w.Linv, b, bb, (int)n, B, s, trtri_hook, &hc));
   if (n > 1) {
     GemmArgs g = one_term(term(lower, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           w.G, b, B, B, 0.0, 0);
     g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)(n - 1);
-    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
   if (a > 0) {
     GemmArgs g = one_term(term(arrow, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           w.H, b, Aa, B, 0.0, 0);
     g.t[0].sA1 = ab; g.t[0].sB1 = bb; g.sC1 = ab; g.nb1 = (int)n;
-    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
   {
     GemmArgs g = one_term(term(w.Linv, b, OP_T, TRI_UPPER, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           diag, b, B, B, 0.0, 1);
     g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)n;
-    BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
   if (a > 0) {
     BTA_TRY(trtri_blocks(tip, a, a * a, w.LtInv, a, a * a, 1, Aa, s));
     BTA_TRY(gemm_run(one_term(term(w.LtInv, a, OP_T, TRI_UPPER, w.LtInv, a, OP_N, TRI_LOWER, Aa,
                                    1.0),
-                              tip, a, Aa, Aa, 0.0, 0), CLS_SELINV, tw, s));
+                              tip, a, Aa, Aa, 0.0, 0), CLS_SELINV, tw, prec, s));
   }
   // Backward sweep.
   for (int64_t i = n - 1; i >= 0; --i) {
@@ -244,7 +251,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
     }
     if (a > 0) {
       // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i
@@ -254,7 +261,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
     }
     // X_ii = M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i  (lower tiles, then mirrored)
     GemmArgs g{};
@@ -263,7 +270,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       g.t[g.nterms++] = term(lower + i * bb, b, OP_T, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
     if (a > 0)
       g.t[g.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
-    if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, s));
+    if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
     BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
   }
   return 0;
@@ -309,11 +316,58 @@ int with_async_ws(size_t bytes, cudaStream_t s, F body) {
   return rc;
 }
 
-size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch) {
-  const int mode = tc_mode_of(g_prec);
+size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch, int prec) {
+  const int mode = tc_mode_of(prec);
   if (!mode || b < 64) return 0;
   const int m = (int)(a > b ? a : b);  // the widest product: b x b, or a x b / a x a blocks
-  return tc_workspace_bytes(mode, m, m, m, (int)(batch < 1 ? 1 : batch));
+  const int k = (int)(((b + 31) / 32 + (a + 31) / 32) * 32);  // two terms concatenated along k
+  return tc_workspace_bytes(mode, m, m, k > m ? k : m, (int)(batch < 1 ? 1 : batch));
+}
+
+// Side streams (and fork/join events) for batched calls, created once per device.
+struct StreamPool {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+};
+std::mutex g_pool_mu;
+StreamPool g_pools[64];
+
+cudaError_t pool_for(int k, StreamPool** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  StreamPool& p = g_pools[dev];
+  if (!p.fork) {
+    e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  while ((int)p.streams.size() < k) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    p.streams.push_back(st);
+    p.join.push_back(ev);
+  }
+  *out = &p;
+  return cudaSuccess;
+}
+
+size_t batch_entry_ws(int64_t n, int64_t b, int64_t a, int prec) {
+  const size_t f = factor_ws(n, b, a, nullptr, nullptr, prec);
+  const size_t s = selinv_ws(n, b, a, nullptr, nullptr, prec);
+  const size_t l = logdet_ws(n, nullptr, nullptr);
+  return std::max(f, std::max(s, l));
+}
+
+double entry_flops(int64_t n, int64_t b, int64_t a) {
+  const double B = (double)b, A = (double)a;
+  return (double)n * (7.0 * B * B * B + 6.0 * A * B * B);
 }
 
 }  // namespace
@@ -325,8 +379,8 @@ int bta_version(void) { return 100; }
 size_t bta_workspace_bytes(int op, int64_t n, int64_t b, int64_t a, int64_t nrhs) {
   if (check_sizes(n, b, a)) return 0;
   switch (op) {
-    case BTA_OP_FACTOR: return factor_ws(n, b, a, nullptr, nullptr);
-    case BTA_OP_SELINV: return selinv_ws(n, b, a, nullptr, nullptr);
+    case BTA_OP_FACTOR: return factor_ws(n, b, a, nullptr, nullptr, g_prec);
+    case BTA_OP_SELINV: return selinv_ws(n, b, a, nullptr, nullptr, g_prec);
     case BTA_OP_SOLVE:
       if (nrhs < 1 || nrhs > 64) return 0;
       return solve_ws(n, b, a, nrhs, nullptr, nullptr);
@@ -341,10 +395,11 @@ int bta_factor_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower, 
   if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
   if (rc) return rc;
   FactorWs w;
-  const size_t need = factor_ws(n, b, a, ws, &w);
+  const int prec = g_prec;
+  const size_t need = factor_ws(n, b, a, ws, &w, prec);
   if (!ws || ((uintptr_t)ws % kAlign)) return -8;
   if (ws_bytes < need) return -9;
-  return factor_impl(n, b, a, diag, lower, arrow, tip, w, (cudaStream_t)stream);
+  return factor_impl(n, b, a, diag, lower, arrow, tip, w, prec, (cudaStream_t)stream);
 }
 
 int bta_factor(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
@@ -352,7 +407,7 @@ int bta_factor(int64_t n, int64_t b, int64_t a, double* diag, double* lower, dou
   int rc = check_sizes(n, b, a);
   if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
   if (rc) return rc;
-  const size_t need = factor_ws(n, b, a, nullptr, nullptr);
+  const size_t need = factor_ws(n, b, a, nullptr, nullptr, g_prec);
   return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
     return bta_factor_ws(n, b, a, diag, lower, arrow, tip, p, need, stream);
   });
@@ -364,10 +419,11 @@ int bta_selinv_ws(int64_t n, int64_t b, int64_t a, double* diag, double* lower, 
   if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
   if (rc) return rc;
   SelinvWs w;
-  const size_t need = selinv_ws(n, b, a, ws, &w);
+  const int prec = g_prec;
+  const size_t need = selinv_ws(n, b, a, ws, &w, prec);
   if (!ws || ((uintptr_t)ws % kAlign)) return -8;
   if (ws_bytes < need) return -9;
-  return selinv_impl(n, b, a, diag, lower, arrow, tip, w, (cudaStream_t)stream);
+  return selinv_impl(n, b, a, diag, lower, arrow, tip, w, prec, (cudaStream_t)stream);
 }
 
 int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
@@ -375,7 +431,7 @@ int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower, dou
   int rc = check_sizes(n, b, a);
   if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
   if (rc) return rc;
-  const size_t need = selinv_ws(n, b, a, nullptr, nullptr);
+  const size_t need = selinv_ws(n, b, a, nullptr, nullptr, g_prec);
   return with_async_ws(need, (cudaStream_t)stream, [&](void* p) {
     return bta_selinv_ws(n, b, a, diag, lower, arrow, tip, p, need, stream);
   });
@@ -438,12 +494,105 @@ int bta_logdet(int64_t n, int64_t b, int64_t a, const double* diag, const double
   });
 }
 
+size_t bta_batch_workspace_bytes(int64_t n, int64_t b, int64_t a, int prec) {
+  if (check_sizes(n, b, a)) return 0;
+  if (prec != BTA_PREC_FP64 && prec != BTA_PREC_OZAKI && prec != BTA_PREC_BF16X3) return 0;
+  return batch_entry_ws(n, b, a, prec);
+}
+
+int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int nstreams,
+                              bta_stream_t stream) {
+  if (count < 1 || count > (1 << 20)) return -1;
+  if (!entries) return -2;
+  if (nstreams < 1 || nstreams > 64) return -3;
+  for (int64_t k = 0; k < count; ++k) {
+    const bta_batch_entry& e = entries[k];
+    if (check_sizes(e.n, e.b, e.a) || check_blocks(e.n, e.a, e.diag, e.lower, e.arrow, e.tip))
+      return -2;
+    if (e.prec != BTA_PREC_FP64 && e.prec != BTA_PREC_OZAKI && e.prec != BTA_PREC_BF16X3) return -2;
+    if (!e.ws || ((uintptr_t)e.ws % kAlign) || e.ws_bytes < batch_entry_ws(e.n, e.b, e.a, e.prec))
+      return -2;
+    if (e.logdet_out && misaligned(e.logdet_out)) return -2;
+  }
+  const cudaStream_t s0 = (cudaStream_t)stream;
+  const int ns = (int)std::min<int64_t>(nstreams, count);
+  StreamPool* pool = nullptr;
+  BTA_TRY(pool_for(ns, &pool));
+  // Largest first, each matrix to the stream with the least work so far.
+  std::vector<int64_t> order(count);
+  for (int64_t k = 0; k < count; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    return entry_flops(entries[x].n, entries[x].b, entries[x].a) >
+           entry_flops(entries[y].n, entries[y].b, entries[y].a);
+  });
+  std::vector<double> load(ns, 0.0);
+  BTA_TRY(cudaEventRecord(pool->fork, s0));
+  for (int i = 0; i < ns; ++i) BTA_TRY(cudaStreamWaitEvent(pool->streams[i], pool->fork, 0));
+  for (int64_t k : order) {
+    const bta_batch_entry& e = entries[k];
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[j] += entry_flops(e.n, e.b, e.a);
+    cudaStream_t st = pool->streams[j];
+    FactorWs fw;
+    factor_ws(e.n, e.b, e.a, e.ws, &fw, e.prec);
+    int rc = factor_impl(e.n, e.b, e.a, e.diag, e.lower, e.arrow, e.tip, fw, e.prec, st);
+    if (rc) return rc;
+    if (e.logdet_out) {
+      LogdetWs lw;
+      logdet_ws(e.n, e.ws, &lw);
+      BTA_TRY(logdet_f64(e.diag, e.n, e.b, e.tip, e.a, lw.partial, e.logdet_out, st));
+    }
+    SelinvWs sw;
+    selinv_ws(e.n, e.b, e.a, e.ws, &sw, e.prec);
+    rc = selinv_impl(e.n, e.b, e.a, e.diag, e.lower, e.arrow, e.tip, sw, e.prec, st);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < ns; ++i) {
+    BTA_TRY(cudaEventRecord(pool->join[i], pool->streams[i]));
+    BTA_TRY(cudaStreamWaitEvent(s0, pool->join[i], 0));
+  }
+  return 0;
+}
+
 int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,
                         bta_stream_t stream) {
   if (!out_dev) return -1;
   if (iters < 1) return -2;
   if (!flops) return -3;
   BTA_TRY(fp64_probe(out_dev, iters, flops, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_grad_blocks(int64_t n, int64_t b, int64_t a, const double* x_diag, const double* x_lower,
+                    const double* x_arrow, const double* x_tip, const double* y, double alpha,
+                    double beta, double* g_diag, double* g_lower, double* g_arrow, double* g_tip,
+                    double* g_x, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (rc) return rc;
+  if (!x_diag || misaligned(x_diag)) return -4;
+  if (n > 1 && (!x_lower || misaligned(x_lower))) return -5;
+  if (a > 0 && (!x_arrow || misaligned(x_arrow))) return -6;
+  if (a > 0 && (!x_tip || misaligned(x_tip))) return -7;
+  if (!y || misaligned(y)) return -8;
+  if (!g_diag || misaligned(g_diag)) return -11;
+  if (n > 1 && (!g_lower || misaligned(g_lower))) return -12;
+  if (a > 0 && (!g_arrow || misaligned(g_arrow))) return -13;
+  if (a > 0 && (!g_tip || misaligned(g_tip))) return -14;
+  if (g_x && misaligned(g_x)) return -15;
+  BTA_TRY(grad_blocks(n, b, a, x_diag, x_lower, x_arrow, x_tip, y, alpha, beta, g_diag, g_lower,
+                      g_arrow, g_tip, g_x, (cudaStream_t)stream));
+  return 0;
+}
+
+int bta_dot(int64_t N, const double* x, const double* y, double* out_dev, void* ws,
+            size_t ws_bytes, bta_stream_t stream) {
+  if (N < 1) return -1;
+  if (!x || misaligned(x)) return -2;
+  if (!y || misaligned(y)) return -3;
+  if (!out_dev || misaligned(out_dev)) return -4;
+  if (!ws || misaligned(ws)) return -5;
+  if (ws_bytes < (size_t)kDotCtas * sizeof(double)) return -6;
+  BTA_TRY(dot_f64(N, x, y, (double*)ws, out_dev, (cudaStream_t)stream));
   return 0;
 }
 

@@ -57,10 +57,12 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          long long info_row0, long long info_rstride,
                          cudaStream_t s);
 // Inverse of lower-triangular blocks: Linv (separate buffer, same layout) =
-// L^{-1}, strict upper triangle zero.
+// L^{-1}, strict upper triangle zero. The doubling products go through `hook`
+// when given (it may run them on the tensor cores), else the FP64 kernels.
+typedef cudaError_t (*GemmHook)(const GemmArgs& g, void* ctx, cudaStream_t s);
 cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Linv,
                          int64_t ldi, int64_t si, int count, int nrow,
-                         cudaStream_t s);
+                         cudaStream_t s, GemmHook hook = nullptr, void* ctx = nullptr);
 // Copy the lower triangle onto the upper one (symmetrize) for `count` blocks.
 cudaError_t mirror_lower(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          cudaStream_t s);
@@ -85,6 +87,17 @@ cudaError_t arrow_gather(const double* arrow, int64_t n, int64_t b, int64_t a,
 cudaError_t arrow_scatter(const double* arrow, int64_t n, int64_t b, int64_t a,
                           const double* xn, int R, double* rhs, cudaStream_t s);
 int arrow_chunks(int64_t n);
+
+// Gradients of alpha log det A + beta x^T A^{-1} x (y = A^{-1} x): blocks
+// G = alpha X - beta y y^T (off-diagonal blocks doubled); gx = 2 beta y (optional).
+cudaError_t grad_blocks(int64_t n, int64_t b, int64_t a, const double* Xd, const double* Xl,
+                        const double* Xa, const double* Xt, const double* y, double alpha,
+                        double beta, double* Gd, double* Gl, double* Ga, double* Gt, double* gx,
+                        cudaStream_t s);
+constexpr int kDotCtas = 608;
+// out = x^T y (deterministic order); partial: kDotCtas doubles.
+cudaError_t dot_f64(int64_t N, const double* x, const double* y, double* partial, double* out,
+                    cudaStream_t s);
 
 // DMMA peak probe; *flops receives the launch's flop count.
 cudaError_t fp64_probe(double* out, long long iters, double* flops, cudaStream_t s);

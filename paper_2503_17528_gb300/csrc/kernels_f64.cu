@@ -142,8 +142,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
         Bs[kk][j] = v;
       }
       __syncthreads();
+      const int kl = min(T, ke - k0);  // a ragged last chunk stops at its last 4-wide k-step
 #pragma unroll
       for (int ks = 0; ks < T; ks += 4) {
+        if (ks >= kl) break;
         const double a0 = As[wm + gq][ks + tq];
         const double a1 = As[wm + 8 + gq][ks + tq];
         const double b0 = Bs[ks + tq][wn + gq];
@@ -208,8 +210,86 @@ static double gemm_alg_flops(const GemmArgs& g) {
   return total * g.nb1 * g.nb2;
 }
 
+// Skinny products (M <= 32 rows, the arrowhead blocks): one CTA per 8-column
+// strip of C and batch entry, 8 warps splitting k; each warp runs m8n8k4 DMMA
+// on row groups of 8 straight from global memory (operands are reused through
+// L1/L2), and the warps' partial sums are added in a fixed order in shared memory.
+constexpr int kSkinnyMaxM = 32;
+
+__global__ void __launch_bounds__(256) gemm_skinny_kernel(GemmArgs g) {
+  __shared__ double red[8][kSkinnyMaxM / 8][64];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int tilesN = (g.N + 7) / 8;
+  long long bid = blockIdx.x;
+  const int tn = (int)(bid % tilesN);
+  bid /= tilesN;
+  const int z1 = (int)(bid % g.nb1), z2 = (int)(bid / g.nb1);
+  const int n0 = tn * 8;
+  const int mg = (g.M + 7) / 8;  // row groups of 8
+  double acc[kSkinnyMaxM / 8][2];
+#pragma unroll
+  for (int r = 0; r < kSkinnyMaxM / 8; ++r) acc[r][0] = acc[r][1] = 0.0;
+  for (int ti = 0; ti < g.nterms; ++ti) {
+    const GemmTerm& t = g.t[ti];
+    const double* A = t.A + (int64_t)z1 * t.sA1 + (int64_t)z2 * t.sA2;
+    const double* B = t.B + (int64_t)z1 * t.sB1 + (int64_t)z2 * t.sB2;
+    int kb = 0, ke = t.K;
+    if (t.triB == TRI_LOWER) kb = max(kb, n0);
+    if (t.triB == TRI_UPPER) ke = min(ke, n0 + 8);
+    // k split across the 8 warps in 4-wide steps
+    const int steps = (ke - kb + 3) / 4;
+    const int per = (steps + 7) / 8;
+    const int s0 = w * per, s1 = min(steps, s0 + per);
+    const int col = n0 + gq;
+    for (int st = s0; st < s1; ++st) {
+      const int k = kb + st * 4 + tq;
+      double bv = 0.0;
+      if (k < ke && col < g.N)
+        bv = t.opB == OP_N ? B[(int64_t)k * t.ldb + col] : B[(int64_t)col * t.ldb + k];
+#pragma unroll
+      for (int r = 0; r < kSkinnyMaxM / 8; ++r) {
+        if (r >= mg) break;
+        const int row = r * 8 + gq;
+        double av = 0.0;
+        const bool in = row < g.M && k < ke;
+        if (in) av = t.opA == OP_N ? A[(int64_t)row * t.lda + k] : A[(int64_t)k * t.lda + row];
+        if (in && t.triA == TRI_LOWER && k > row) av = 0.0;
+        if (in && t.triA == TRI_UPPER && k < row) av = 0.0;
+        dmma_8x8x4(acc[r], scale_by(av, t.alpha), bv);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kSkinnyMaxM / 8; ++r) {
+    red[w][r][lane * 2] = acc[r][0];
+    red[w][r][lane * 2 + 1] = acc[r][1];
+  }
+  __syncthreads();
+  double* C = g.C + (int64_t)z1 * g.sC1 + (int64_t)z2 * g.sC2;
+  for (int e = tid; e < mg * 64; e += 256) {
+    const int r = e / 64, q = e % 64;  // q = lane*2 + j -> row r*8 + lane/4, col n0 + 2*(lane%4) + j
+    const int ln = q / 2, j = q % 2;
+    const int row = r * 8 + (ln >> 2), c = n0 + 2 * (ln & 3) + j;
+    if (row >= g.M || c >= g.N) continue;
+    if (g.lowerC && c > row) continue;
+    double v = 0.0;
+    for (int ww = 0; ww < 8; ++ww) v += red[ww][r][q];
+    double* p = C + (int64_t)row * g.ldc + c;
+    if (g.beta != 0.0) v += g.beta * *p;
+    *p = v;
+  }
+}
+
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
+  if (g.M <= kSkinnyMaxM && g.N >= 64) {
+    const long long grid = (long long)((g.N + 7) / 8) * g.nb1 * g.nb2;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    TimedLaunch tl(K_GEMM, timing_on() ? gemm_alg_flops(g) : 0.0, s);
+    gemm_skinny_kernel<<<(unsigned)grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+  }
   const long long tm = (g.M + T - 1) / T, tn = (g.N + T - 1) / T;
   const long long tiles = (g.lowerC && g.M == g.N) ? tm * (tm + 1) / 2 : tm * tn;
   const long long grid = tiles * g.nb1 * g.nb2;
@@ -405,7 +485,8 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
 }
 
 cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Li, int64_t ldi,
-                         int64_t si, int count, int nrow, cudaStream_t s) {
+                         int64_t si, int count, int nrow, cudaStream_t s, GemmHook hook,
+                         void* ctx) {
   if (count <= 0 || nrow <= 0) return cudaSuccess;
   const int nt = (nrow + T - 1) / T;
   for (int c0 = 0; c0 < count; c0 += 65535) {
@@ -438,7 +519,7 @@ cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Li, i
         g1.nterms = 1;
         g1.C = Xc + (int64_t)o * ldi + o + sz; g1.ldc = ldi; g1.sC1 = pstride_i; g1.sC2 = si;
         g1.M = sz; g1.N = s2; g1.beta = 0.0; g1.lowerC = 0; g1.nb1 = pairs; g1.nb2 = cnt;
-        cudaError_t e = gemm_f64(g1, s);
+        cudaError_t e = hook ? hook(g1, ctx, s) : gemm_f64(g1, s);
         if (e != cudaSuccess) return e;
         // X21 (s2 x sz) = -X22 (s2 x s2, lower) * Tmp (s2 x sz)
         GemmArgs g2{};
@@ -449,7 +530,7 @@ cudaError_t trtri_blocks(const double* L, int64_t ldl, int64_t sl, double* Li, i
         g2.nterms = 1;
         g2.C = Xc + (int64_t)(o + sz) * ldi + o; g2.ldc = ldi; g2.sC1 = pstride_i; g2.sC2 = si;
         g2.M = s2; g2.N = sz; g2.beta = 0.0; g2.lowerC = 0; g2.nb1 = pairs; g2.nb2 = cnt;
-        e = gemm_f64(g2, s);
+        e = hook ? hook(g2, ctx, s) : gemm_f64(g2, s);
         if (e != cudaSuccess) return e;
       }
     }
@@ -785,6 +866,82 @@ cudaError_t arrow_scatter(const double* arrow, int64_t n, int64_t b, int64_t a, 
   if (a <= 0) return cudaSuccess;
   TimedLaunch tl(K_ARROW, 2.0 * n * a * b * R, s);
   arrow_scatter_kernel<<<ceil_div(n * b, 256), 256, 0, s>>>(arrow, n, b, a, xn, R, rhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gradient assembly for alpha log det A + beta x^T A^{-1} x with respect to the
+// stored blocks: G = alpha X - beta y y^T on the pattern, doubled on the
+// off-diagonal (lower, arrow) blocks, which stand for themselves and their
+// transposes; and with respect to x: 2 beta y.
+// ---------------------------------------------------------------------------
+__global__ void grad_blocks_kernel(int64_t n, int64_t b, int64_t a, const double* Xd,
+                                   const double* Xl, const double* Xa, const double* Xt,
+                                   const double* y, double alpha, double qbeta, double* Gd,
+                                   double* Gl, double* Ga, double* Gt, double* gx) {
+  const int64_t nd = n * b * b, nl = (n - 1) * b * b, na = n * a * b, nt = a * a;
+  const int64_t total = nd + nl + na + nt;
+  const double beta = -qbeta;
+  if (gx)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * b + a;
+         e += (int64_t)gridDim.x * blockDim.x)
+      gx[e] = 2.0 * qbeta * y[e];
+  const double* yn = y + n * b;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nd) {
+      const int64_t i = e / (b * b), r = (e / b) % b, c = e % b;
+      Gd[e] = alpha * Xd[e] + beta * y[i * b + r] * y[i * b + c];
+    } else if (e < nd + nl) {
+      const int64_t f = e - nd, i = f / (b * b), r = (f / b) % b, c = f % b;
+      Gl[f] = 2.0 * (alpha * Xl[f] + beta * y[(i + 1) * b + r] * y[i * b + c]);
+    } else if (e < nd + nl + na) {
+      const int64_t f = e - nd - nl, i = f / (a * b), r = (f / b) % a, c = f % b;
+      Ga[f] = 2.0 * (alpha * Xa[f] + beta * yn[r] * y[i * b + c]);
+    } else {
+      const int64_t f = e - nd - nl - na, r = f / a, c = f % a;
+      Gt[f] = alpha * Xt[f] + beta * yn[r] * yn[c];
+    }
+  }
+}
+
+cudaError_t grad_blocks(int64_t n, int64_t b, int64_t a, const double* Xd, const double* Xl,
+                        const double* Xa, const double* Xt, const double* y, double alpha,
+                        double beta, double* Gd, double* Gl, double* Ga, double* Gt, double* gx,
+                        cudaStream_t s) {
+  grad_blocks_kernel<<<1216, 256, 0, s>>>(n, b, a, Xd, Xl, Xa, Xt, y, alpha, beta, Gd, Gl, Ga, Gt,
+                                          gx);
+  return cudaGetLastError();
+}
+
+// Deterministic dot product x^T y (per-CTA tree sums, then CTAs in order).
+__global__ void __launch_bounds__(256) dot_partial_kernel(int64_t N, const double* x,
+                                                          const double* y, double* partial) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N; e += (int64_t)gridDim.x * 256)
+    acc = fma(x[e], y[e], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void ordered_sum_kernel(const double* partial, int count, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int z = 0; z < count; ++z) s += partial[z];
+    *out = s;
+  }
+}
+
+cudaError_t dot_f64(int64_t N, const double* x, const double* y, double* partial, double* out,
+                    cudaStream_t s) {
+  dot_partial_kernel<<<kDotCtas, 256, 0, s>>>(N, x, y, partial);
+  ordered_sum_kernel<<<1, 32, 0, s>>>(partial, kDotCtas, out);
   return cudaGetLastError();
 }
 

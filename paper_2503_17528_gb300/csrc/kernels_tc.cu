@@ -137,6 +137,18 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Output addressing of a chunk of a (two-level) batch.
+struct COut {
+  double* C;
+  int64_t ldc, s1, s2;
+  int nb1, zbase;
+};
+
+__device__ __forceinline__ double* c_base(const COut& c, int zl) {
+  const int z = c.zbase + zl;
+  return c.C + (int64_t)(z % c.nb1) * c.s1 + (int64_t)(z / c.nb1) * c.s2;
+}
+
 struct TcArgs {
   int M, N;          // logical output size
   int Kc;            // padded k extent of the slices (multiple of BK)
@@ -152,8 +164,7 @@ struct TcArgs {
   int nb;            // batch count
   const double* sa;  // [nb][Mpad] row scales of A
   const double* sb;  // [nb][Npad] column scales of B
-  double* C;
-  int64_t ldc, sC;
+  COut co;
   double alpha, beta;
 };
 
@@ -291,35 +302,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         // Exact groups -> integers, all groups -> one int64 in units of 2^-49.
         long long* Tz = g.T + ((int64_t)z * g.Mpad + row) * g.Npad;
         for (int c0 = 0; c0 < BN; c0 += 16) {
-          uint32_t r[kOzGroups][16];
+          long long acc[16];
 #pragma unroll
-          for (int gi = 0; gi < kOzGroups; ++gi)
-            if (gi < ngroups) tmem_ld16(lane_base + gi * BN + c0, r[gi]);
-          tmem_wait_ld();
+          for (int j = 0; j < 16; ++j) acc[j] = 0;
+#pragma unroll
+          for (int gi = 0; gi < kOzGroups; ++gi) {
+            if (gi >= ngroups) break;  // warp-uniform
+            uint32_t r[16];
+            tmem_ld16(lane_base + gi * BN + c0, r);
+            tmem_wait_ld();
+            // group gi holds sum d d' 2^-7(gi+2): exact groups -> integers, scaled to 2^-49 units;
+            // the shared group is rounded to the 2^-49 quantum
+            const float up = __int_as_float((127 + (gi < kOzGroups - 1 ? 7 * (gi + 2) : kFixShift)) << 23);
+            const int sh = gi < kOzGroups - 1 ? kFixShift - 7 * (gi + 2) : 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] += __float2ll_rn(__uint_as_float(r[j]) * up) << sh;
+          }
           if (row < g.M) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              long long acc = 0;
-#pragma unroll
-              for (int gi = 0; gi < kOzGroups; ++gi) {
-                if (gi >= ngroups) break;
-                const float v = __uint_as_float(r[gi][j]);
-                // group gi holds sum d*d' 2^-7(gi+2); scale to units of 2^-49
-                // 2^(7(gi+2)) as an FP32 bit pattern: exact power-of-two scaling
-                if (gi < kOzGroups - 1) {
-                  const long long iv =
-                      __float2ll_rn(v * __int_as_float((127 + 7 * (gi + 2)) << 23));  // exact integer
-                  acc += iv << (kFixShift - 7 * (gi + 2));
-                } else {
-                  acc += __float2ll_rn(v * __int_as_float((127 + kFixShift) << 23));  // rounded to the quantum
-                }
-              }
-              if (acc) atomicAdd((unsigned long long*)(Tz + n0 + c0 + j), (unsigned long long)acc);
-            }
+            for (int j = 0; j < 16; ++j)
+              if (acc[j]) atomicAdd((unsigned long long*)(Tz + n0 + c0 + j), (unsigned long long)acc[j]);
           }
         }
       } else {
-        double* Cz = g.C + (int64_t)z * g.sC;
+        double* Cz = c_base(g.co, z);
         for (int c0 = 0; c0 < BN; c0 += 16) {
           uint32_t r[16];
           tmem_ld16(lane_base + c0, r);
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < 16; ++j) {
               const int col = n0 + c0 + j;
               if (col >= g.N) break;
-              double* p = Cz + (int64_t)row * g.ldc + col;
+              double* p = Cz + (int64_t)row * g.co.ldc + col;
               double out = g.alpha * (double)__uint_as_float(r[j]);
               if (g.beta != 0.0) out += g.beta * *p;
               *p = out;
@@ -341,10 +347,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // X3 with an empty k-range: C = beta * C on this tile.
     const int row = m0 + warp * 32 + lane;
-    double* Cz = g.C + (int64_t)z * g.sC;
+    double* Cz = c_base(g.co, z);
     if (row < g.M)
       for (int c = 0; c < BN && n0 + c < g.N; ++c) {
-        double* p = Cz + (int64_t)row * g.ldc + n0 + c;
+        double* p = Cz + (int64_t)row * g.co.ldc + n0 + c;
         *p = g.beta != 0.0 ? g.beta * *p : 0.0;
       }
   }
@@ -361,83 +367,98 @@ __global__ void __launch_bounds__(kThreads, 1)
 // element (r, k) of batch z is X[z*sz + r*sr + (k0 + k)*sk].
 // ---------------------------------------------------------------------------
 struct SplitArgs {
-  const double* X;
-  int64_t sr, sk, sz;
-  int R, Kc, k0, Kp;    // rows, k extent of the chunk, global k offset, padded k
+  const double* X;      // part base
+  int64_t sr, sk;       // element (r, k) of a batch entry at X[r*sr + k*sk]
+  int64_t s1, s2;       // batch strides: entry z -> (z % nb1) * s1 + (z / nb1) * s2
+  int nb1, zbase;       // flattened batch decomposition; first entry of this chunk
+  int R, Kc;            // rows, k extent of this part
+  int kout0, Kp;        // first output column of the part, padded row length of the slices
   int Rpad, s, mode, nb;
+  int mask;             // structural zeros: 0 none, 1 where k > r, 2 where k < r
   __nv_bfloat16* out;   // [nb][s][Rpad][Kp]
   double* scale;        // [nb][Rpad]
-  unsigned long long* rowmax;  // [nb][Rpad] scratch (|x| bit patterns)
+  unsigned long long* rowmax;  // [nb][Rpad], |x| bit patterns, zeroed before the first part
 };
 
-// Row maxima of |x| as FP64 bit patterns (order-preserving for non-negative values).
+__device__ __forceinline__ bool masked(const SplitArgs& a, int r, int k) {
+  return (a.mask == 1 && k > r) || (a.mask == 2 && k < r);
+}
+
+__device__ __forceinline__ const double* part_base(const SplitArgs& a, int zl) {
+  const int z = a.zbase + zl;
+  return a.X + (int64_t)(z % a.nb1) * a.s1 + (int64_t)(z / a.nb1) * a.s2;
+}
+
+// Row maxima of |x| (FP64 bit patterns are order-preserving for non-negative
+// values): each CTA reduces 32 rows over a 256-wide k slab and merges with atomicMax.
 __global__ void __launch_bounds__(256) split_rowmax_kernel(SplitArgs a) {
-  const int z = blockIdx.y;
-  const int r0 = blockIdx.x * 32;
-  const double* Xz = a.X + (int64_t)z * a.sz;
+  const int zl = blockIdx.z;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 256;
+  const double* Xz = part_base(a, zl);
   __shared__ unsigned long long red[8][32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  unsigned long long m = 0;
+  const int kend = min(a.Kc, k0 + 256);
   if (a.sk == 1) {
-    // rows contiguous in k: warp w takes rows r0 + w, w + 8, ...; lanes stride k
+    // k contiguous: warp w takes rows r0 + w + 8j, lanes stride k
     for (int rr = w; rr < 32; rr += 8) {
       const int r = r0 + rr;
       unsigned long long mr = 0;
       if (r < a.R)
-        for (int k = lane; k < a.Kc; k += 32) {
-          const unsigned long long b =
-              (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + a.k0 + k]) & 0x7fffffffffffffffull;
-          mr = b > mr ? b : mr;
+        for (int k = k0 + lane; k < kend; k += 32) {
+          if (masked(a, r, k)) continue;
+          const unsigned long long v =
+              (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + k]) & 0x7fffffffffffffffull;
+          mr = v > mr ? v : mr;
         }
       for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o = __shfl_xor_sync(0xffffffffu, mr, off);
         mr = o > mr ? o : mr;
       }
-      if (lane == 0) red[0][rr] = mr;  // reuse: slot [0][row]
+      if (lane == 0 && r < a.R && mr) atomicMax(&a.rowmax[(int64_t)zl * a.Rpad + r], mr);
     }
-    __syncthreads();
-    if (tid < 32 && r0 + tid < a.Rpad)
-      a.rowmax[(int64_t)z * a.Rpad + r0 + tid] = r0 + tid < a.R ? red[0][tid] : 0ull;
   } else {
-    // rows contiguous across r: lane = row, warps split k
+    // rows contiguous: lane = row, warps split the slab
     const int r = r0 + lane;
+    unsigned long long m = 0;
     if (r < a.R)
-      for (int k = w; k < a.Kc; k += 8) {
-        const unsigned long long b =
-            (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + (int64_t)(a.k0 + k) * a.sk]) &
+      for (int k = k0 + w; k < kend; k += 8) {
+        if (masked(a, r, k)) continue;
+        const unsigned long long v =
+            (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + (int64_t)k * a.sk]) &
             0x7fffffffffffffffull;
-        m = b > m ? b : m;
+        m = v > m ? v : m;
       }
     red[w][lane] = m;
     __syncthreads();
     if (w == 0) {
       for (int ww = 1; ww < 8; ++ww) m = red[ww][lane] > m ? red[ww][lane] : m;
-      if (r < a.Rpad) a.rowmax[(int64_t)z * a.Rpad + r] = r < a.R ? m : 0ull;
+      if (r < a.R && m) atomicMax(&a.rowmax[(int64_t)zl * a.Rpad + r], m);
     }
   }
 }
 
-// Digit slices (OZ) or hi/lo slices (X3) of a 32 x 32 tile, plus row scales.
-__global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a) {
+// Digit slices (OZ) or hi/lo slices (X3) of a 32 x 32 tile of one part. The
+// first part also writes the row scales (after every part's row maxima).
+__global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a, int write_scale) {
   __shared__ double tile[32][33];
-  const int z = blockIdx.z;
+  const int zl = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const double* Xz = a.X + (int64_t)z * a.sz;
+  const double* Xz = part_base(a, zl);
   const int tid = threadIdx.x;
-  // Coalesced load along whichever dimension is contiguous.
   for (int e = tid; e < 32 * 32; e += 256) {
     int i, j;
     if (a.sk == 1) { i = e / 32; j = e % 32; } else { j = e / 32; i = e % 32; }
     const int r = r0 + i, k = c0 + j;
-    tile[i][j] = (r < a.R && k < a.Kc) ? Xz[(int64_t)r * a.sr + (int64_t)(a.k0 + k) * a.sk] : 0.0;
+    tile[i][j] = (r < a.R && k < a.Kc && !masked(a, r, k)) ? Xz[(int64_t)r * a.sr + (int64_t)k * a.sk] : 0.0;
   }
   __syncthreads();
+  const int kw = ((a.Kc + 31) / 32) * 32;  // this part's padded width
   for (int e = tid; e < 32 * 32; e += 256) {
     const int i = e / 32, j = e % 32;
     const int r = r0 + i, k = c0 + j;
-    if (r >= a.Rpad || k >= a.Kp) continue;
+    if (r >= a.Rpad || k >= kw) continue;
     const double x = tile[i][j];
-    __nv_bfloat16* o = a.out + (((int64_t)z * a.s) * a.Rpad + r) * a.Kp + k;
+    __nv_bfloat16* o = a.out + (((int64_t)zl * a.s) * a.Rpad + r) * a.Kp + a.kout0 + k;
     const int64_t plane = (int64_t)a.Rpad * a.Kp;
     if (a.mode == TC_X3) {
       const float xf = (float)x;
@@ -448,18 +469,18 @@ __global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a) {
       continue;
     }
     // Ozaki digits by integer arithmetic on the FP64 fields.
-    const unsigned long long mb = r < a.R ? a.rowmax[(int64_t)z * a.Rpad + r] : 0ull;
+    const unsigned long long mb = r < a.R ? a.rowmax[(int64_t)zl * a.Rpad + r] : 0ull;
     const int emax = (int)(mb >> 52);           // biased exponent of the row max
     const long long bits = __double_as_longlong(x);
     const int ex = (int)((bits >> 52) & 0x7ff);
     long long Y = 0;
     if (emax > 0 && emax < 2047 && ex > 0) {
       // |x| = M 2^(ex-1075); row scale 2^e with e = emax - 1021 puts |x| 2^-e below 1/2;
-      // Y = round(|x| 2^(7s - e)) = round(M 2^sh).
+      // Y = round(|x| 2^(7s - e)) = round(M 2^sh), sh <= 7s - 54 < 0.
       const long long M = (bits & 0x000fffffffffffffll) | 0x0010000000000000ll;
       const int e = emax - 1021;
       const int sh = ex - 1075 + 7 * a.s - e;
-      if (sh >= 0) Y = M << sh;                 // cannot overflow: Y < 2^(7s-1)
+      if (sh >= 0) Y = M << sh;
       else if (sh > -64) Y = (M + (1ll << (-sh - 1))) >> (-sh);
       if (bits < 0) Y = -Y;
     }
@@ -477,39 +498,35 @@ __global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a) {
       sc *= 1.0f / 128.0f;
     }
   }
-  if (a.mode == TC_OZ && blockIdx.x == 0 && tid < 32) {
+  if (write_scale && blockIdx.x == 0 && tid < 32) {
     const int r = r0 + tid;
     if (r < a.Rpad) {
-      double sc = 0.0;
-      if (r < a.R) {
-        const unsigned long long mb = a.rowmax[(int64_t)z * a.Rpad + r];
+      double sc = 1.0;
+      if (a.mode == TC_OZ && r < a.R) {
+        const unsigned long long mb = a.rowmax[(int64_t)zl * a.Rpad + r];
         const int emax = (int)(mb >> 52);
         if (emax == 2047) sc = __longlong_as_double(0x7ff8000000000000ll);  // NaN/Inf row
         else if (emax > 0) sc = ldexp(1.0, emax - 1021);
-        else sc = 1.0;  // zero (or subnormal-only) row: digits are zero
       }
-      a.scale[(int64_t)z * a.Rpad + r] = sc;
+      a.scale[(int64_t)zl * a.Rpad + r] = sc;
     }
   }
-  if (a.mode == TC_X3 && blockIdx.x == 0 && tid < 32 && r0 + tid < a.Rpad)
-    a.scale[(int64_t)z * a.Rpad + r0 + tid] = 1.0;
 }
 
 // C = alpha * T 2^-49 sa_i sb_j + beta * C on the elements the GEMM computed.
 __global__ void __launch_bounds__(256) tc_finalize_kernel(const long long* T, int M, int N, int Mpad,
                                                           int Npad, const double* sa,
-                                                          const double* sb, double* C, int64_t ldc,
-                                                          int64_t sC, double alpha, double beta,
-                                                          int lowerC) {
-  const int z = blockIdx.y;
+                                                          const double* sb, COut co, double alpha,
+                                                          double beta, int lowerC) {
+  const int zl = blockIdx.y;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)M * N) return;
   const int i = (int)(e / N), j = (int)(e % N);
   if (lowerC && (j / BN) * BN > (i / BM) * BM + BM - 1) return;
-  const double v = (double)T[((int64_t)z * Mpad + i) * Npad + j];
+  const double v = (double)T[((int64_t)zl * Mpad + i) * Npad + j];
   const double q = 1.0 / (double)(1ll << kFixShift);  // 2^-49, exact
-  double out = (v * q) * (alpha * sa[(int64_t)z * Mpad + i]) * sb[(int64_t)z * Npad + j];
-  double* p = C + (int64_t)z * sC + (int64_t)i * ldc + j;
+  double out = (v * q) * (alpha * sa[(int64_t)zl * Mpad + i]) * sb[(int64_t)zl * Npad + j];
+  double* p = c_base(co, zl) + (int64_t)i * co.ldc + j;
   if (beta != 0.0) out += beta * *p;
   *p = out;
 }
@@ -579,33 +596,84 @@ size_t tc_workspace_bytes(int mode, int M, int N, int K, int batch) {
   return tc_chunk_bytes(mode, M, N, K, batch < c ? batch : c);
 }
 
-static cudaError_t split_operand(const double* X, int64_t sr, int64_t sk, int64_t sz, int R, int Kc,
-                                 int Kp, int Rpad, int s, int mode, int nb, __nv_bfloat16* out,
-                                 double* scale, unsigned long long* rowmax, cudaStream_t st) {
-  SplitArgs a{};
-  a.X = X; a.sr = sr; a.sk = sk; a.sz = sz; a.R = R; a.Kc = Kc; a.k0 = 0; a.Kp = Kp;
-  a.Rpad = Rpad; a.s = s; a.mode = mode; a.nb = nb; a.out = out; a.scale = scale; a.rowmax = rowmax;
-  if (mode == TC_OZ) split_rowmax_kernel<<<dim3((Rpad + 31) / 32, nb), 256, 0, st>>>(a);
-  split_digits_kernel<<<dim3((Kp + 31) / 32, (Rpad + 31) / 32, nb), 256, 0, st>>>(a);
+// One operand part along k: element (r, k) at X[r*sr + k*sk] plus batch offsets.
+struct Part {
+  const double* X;
+  int64_t sr, sk, s1, s2;
+  int K;
+  int mask;  // see SplitArgs::mask
+};
+
+static cudaError_t split_parts(const Part* parts, int np, int nb1, int zbase, int R, int Kp, int Rpad,
+                               int s, int mode, int nb, __nv_bfloat16* out, double* scale,
+                               unsigned long long* rowmax, cudaStream_t st) {
+  TimedLaunch tl(K_TC_SPLIT, 0.0, st);
+  SplitArgs a[2];
+  int k0 = 0;
+  for (int i = 0; i < np; ++i) {
+    a[i] = SplitArgs{};
+    a[i].X = parts[i].X; a[i].sr = parts[i].sr; a[i].sk = parts[i].sk;
+    a[i].s1 = parts[i].s1; a[i].s2 = parts[i].s2; a[i].nb1 = nb1; a[i].zbase = zbase;
+    a[i].R = R; a[i].Kc = parts[i].K; a[i].kout0 = k0; a[i].Kp = Kp;
+    a[i].Rpad = Rpad; a[i].s = s; a[i].mode = mode; a[i].nb = nb;
+    a[i].out = out; a[i].scale = scale; a[i].rowmax = rowmax; a[i].mask = parts[i].mask;
+    k0 += (int)rup(parts[i].K, BK);
+  }
+  if (mode == TC_OZ) {
+    cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)nb * Rpad * 8, st);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < np; ++i)
+      split_rowmax_kernel<<<dim3((parts[i].K + 255) / 256, (Rpad + 31) / 32, nb), 256, 0, st>>>(a[i]);
+  }
+  for (int i = 0; i < np; ++i)
+    split_digits_kernel<<<dim3((unsigned)((rup(parts[i].K, BK) + 31) / 32), (Rpad + 31) / 32, nb), 256, 0,
+                          st>>>(a[i], i == 0);
   return cudaGetLastError();
 }
 
 static int g_smem_attr_set = 0;
 
 cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (g.nterms != 1) return cudaErrorInvalidValue;
-  const GemmTerm& t = g.t[0];
+  if (g.nterms < 1 || g.nterms > 2) return cudaErrorInvalidValue;
+  // Two terms are one product over the concatenated k range when they share alpha
+  // and neither operand is triangular; otherwise they run one after the other.
+  const bool concat = g.nterms == 2 && g.t[0].alpha == g.t[1].alpha && g.t[0].triA == TRI_NONE &&
+                      g.t[0].triB == TRI_NONE && g.t[1].triA == TRI_NONE && g.t[1].triB == TRI_NONE;
+  if (g.nterms == 2 && !concat) {
+    GemmArgs g0 = g, g1 = g;
+    g0.nterms = 1;
+    g1.t[0] = g.t[1];
+    g1.nterms = 1;
+    g1.beta = 1.0;
+    cudaError_t e = gemm_tc(g0, mode, ws, ws_bytes, s);
+    return e != cudaSuccess ? e : gemm_tc(g1, mode, ws, ws_bytes, s);
+  }
   const int S = tc_slices(mode);
-  const int M = g.M, N = g.N, K = t.K;
-  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  if (K > 16384) return cudaErrorInvalidValue;  // int64 accumulator headroom
-  const int Mp = (int)rup(M, BM), Np = (int)rup(N, BN), Kp = (int)rup(K, BK);
+  const int M = g.M, N = g.N;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  Part pa[2], pb[2];
+  int Kp = 0;
+  for (int i = 0; i < g.nterms; ++i) {
+    const GemmTerm& t = g.t[i];
+    // op(A) element (m, k); op(B)^T element (n, k)
+    // Structural zeros are applied while splitting: triangular operands may hold
+    // anything in their zero parts. op(A) row m: LOWER -> k > m, UPPER -> k < m;
+    // op(B)^T row n: LOWER (zero for k < n), UPPER (zero for k > n).
+    const int ma = t.triA == TRI_LOWER ? 1 : (t.triA == TRI_UPPER ? 2 : 0);
+    const int mb = t.triB == TRI_LOWER ? 2 : (t.triB == TRI_UPPER ? 1 : 0);
+    pa[i] = Part{t.A, t.opA == OP_N ? t.lda : 1, t.opA == OP_N ? 1 : t.lda, t.sA1, t.sA2, t.K, ma};
+    pb[i] = Part{t.B, t.opB == OP_N ? 1 : t.ldb, t.opB == OP_N ? t.ldb : 1, t.sB1, t.sB2, t.K, mb};
+    Kp += (int)rup(t.K, BK);
+  }
+  if (Kp <= 0) return cudaSuccess;
+  if (Kp > 16384) return cudaErrorInvalidValue;  // int64 accumulator headroom
+  const int Mp = (int)rup(M, BM), Np = (int)rup(N, BN);
   const int total = g.nb1 * g.nb2;
   // Batch entries per pass: as many as the design size and the workspace allow.
-  int chunk_nb = tc_batch_chunk(M, N, K);
+  int chunk_nb = tc_batch_chunk(M, N, Kp);
   if (chunk_nb > total) chunk_nb = total;
-  while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, K, chunk_nb) > ws_bytes) --chunk_nb;
-  if (tc_chunk_bytes(mode, M, N, K, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
+  while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) --chunk_nb;
+  if (tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
   // Dynamic shared memory: the opt-in limit less the kernel's static shared memory.
   static size_t dyn_limit = 0;
   if (!dyn_limit) {
@@ -630,15 +698,9 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     if (e != cudaSuccess) return e;
     g_smem_attr_set = (int)smem;
   }
-
-  // Operand strides: op(A) element (m, k); op(B)^T element (n, k).
-  const int64_t a_sr = t.opA == OP_N ? t.lda : 1, a_sk = t.opA == OP_N ? 1 : t.lda;
-  const int64_t b_sr = t.opB == OP_N ? 1 : t.ldb, b_sk = t.opB == OP_N ? t.ldb : 1;
   const int unitk = mode == TC_OZ ? kUnitK : Kp;
   const int nunits = (Kp + unitk - 1) / unitk;
-  // Batch index: one stride dimension (callers use nb2 == 1, or nb1 == 1).
-  const int64_t bsA = g.nb2 == 1 ? t.sA1 : t.sA2, bsB = g.nb2 == 1 ? t.sB1 : t.sB2;
-  const int64_t bsC = g.nb2 == 1 ? g.sC1 : g.sC2;
+  const GemmTerm& t0 = g.t[0];
 
   for (int c0 = 0; c0 < total; c0 += chunk_nb) {
     const int nb = total - c0 < chunk_nb ? total - c0 : chunk_nb;
@@ -653,12 +715,9 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     unsigned long long* rmB = rmA + (int64_t)nb * Mp;
     w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
     long long* Tacc = (long long*)w;
-    const double* A0 = t.A + (int64_t)c0 * bsA;
-    const double* B0 = t.B + (int64_t)c0 * bsB;
-    double* C0 = g.C + (int64_t)c0 * bsC;
-    cudaError_t e = split_operand(A0, a_sr, a_sk, bsA, M, K, Kp, Mp, S, mode, nb, As, sa, rmA, s);
+    cudaError_t e = split_parts(pa, g.nterms, g.nb1, c0, M, Kp, Mp, S, mode, nb, As, sa, rmA, s);
     if (e != cudaSuccess) return e;
-    e = split_operand(B0, b_sr, b_sk, bsB, N, K, Kp, Np, S, mode, nb, Bs, sb, rmB, s);
+    e = split_parts(pb, g.nterms, g.nb1, c0, N, Kp, Np, S, mode, nb, Bs, sb, rmB, s);
     if (e != cudaSuccess) return e;
     if (mode == TC_OZ) {
       e = cudaMemsetAsync(Tacc, 0, (size_t)nb * Mp * Np * 8, s);
@@ -671,21 +730,26 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     TcArgs a{};
     a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.T = Tacc;
     a.s = S; a.mode = mode; a.Mpad = Mp; a.Npad = Np;
-    a.nstages = nstages; a.triA = t.triA; a.triB = t.triB; a.lowerC = g.lowerC; a.nb = nb;
+    a.nstages = nstages; a.lowerC = g.lowerC; a.nb = nb;
+    a.triA = g.nterms == 1 ? t0.triA : TRI_NONE;
+    a.triB = g.nterms == 1 ? t0.triB : TRI_NONE;
     a.sa = sa; a.sb = sb;
-    a.C = C0; a.ldc = g.ldc; a.sC = bsC;
-    a.alpha = t.alpha; a.beta = g.beta;
+    a.co = COut{g.C, g.ldc, g.sC1, g.sC2, g.nb1, c0};
+    a.alpha = t0.alpha; a.beta = g.beta;
     const long long grid = (long long)(Mp / BM) * (Np / BN) * nunits * nb;
     {
-      TimedLaunch tl(K_GEMM_TC, 2.0 * M * N * (double)K * nb * (g.lowerC && M == N ? 0.5 : 1.0), s);
+      double fl = 0.0;
+      for (int i = 0; i < g.nterms; ++i) fl += 2.0 * M * N * (double)g.t[i].K;
+      TimedLaunch tl(K_GEMM_TC, fl * nb * (g.lowerC && M == N ? 0.5 : 1.0), s);
       tc_gemm_kernel<<<(unsigned)grid, kThreads, smem, s>>>(mA, mB, a);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     if (mode == TC_OZ) {
       const int64_t elems = (int64_t)M * N;
+      TimedLaunch tl(K_TC_FINAL, 0.0, s);
       tc_finalize_kernel<<<dim3((unsigned)((elems + 255) / 256), nb), 256, 0, s>>>(
-          Tacc, M, N, Mp, Np, sa, sb, C0, g.ldc, bsC, t.alpha, g.beta, g.lowerC);
+          Tacc, M, N, Mp, Np, sa, sb, a.co, t0.alpha, g.beta, g.lowerC);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -21,6 +21,8 @@ enum KernelId {
   K_ARROW,
   K_PROBE,
   K_GEMM_TC,
+  K_TC_SPLIT,
+  K_TC_FINAL,
   K_COUNT
 };
 

@@ -1,0 +1,74 @@
+"""Autotuner for the batched form: measures every (streams, engine policy)
+candidate on the actual batch and caches the fastest per device and batch
+signature (count and the multiset of (b, a)) in tuning_cache.json beside this
+file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from .batched import POLICIES, Batch
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
+STREAMS = (1, 4, 8, 16, 32)
+
+
+def signature(mats) -> str:
+    name = torch.cuda.get_device_name(mats[0][0].device)
+    shapes = sorted((int(d.shape[1]), int(t.shape[0])) for d, _, _, t in mats)
+    return f"{name}|{len(mats)}|{shapes}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(mats):
+    return _load().get(signature(mats))
+
+
+def tune(mats, pristine, policies=None, streams=STREAMS, reps=2, save=True):
+    """mats: working tensors (overwritten); pristine: matching copies to restore.
+    Returns {"nstreams", "policy", "ms", "table"} and stores it in the cache."""
+    policies = list(policies or POLICIES)
+    table = []
+
+    def restore():
+        for w, p in zip(mats, pristine):
+            for x, y in zip(w, p):
+                if x is not None and x.numel():
+                    x.copy_(y)
+
+    for pol in policies:
+        for ns in streams:
+            batch = Batch(mats, policy=pol, nstreams=ns)
+            restore()
+            batch.run()
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(reps):
+                restore()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                batch.run()
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            table.append({"policy": pol, "nstreams": ns, "ms": min(times)})
+    best = min(table, key=lambda r: r["ms"])
+    res = {"nstreams": best["nstreams"], "policy": best["policy"], "ms": best["ms"], "table": table}
+    if save:
+        cache = _load()
+        cache[signature(mats)] = res
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    restore()
+    return res
