@@ -180,6 +180,34 @@ def cpu_oracle_sample(w, arrays, target_s=8.0, max_blocks=None):
     return per_full, desc, os.cpu_count()
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank factors its own seeded matrix (independent problems)."""
+    return rank
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The job's time is the slowest rank's (all_reduce MAX; no-op for one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_batch(flops, world: int):
+    """Largest-first greedy assignment of independent matrices to ranks (by
+    algorithmic flops); returns one index list per rank. No data crosses ranks."""
+    order = sorted(range(len(flops)), key=lambda k: -flops[k])
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda j: load[j])
+        parts[r].append(k)
+        load[r] += flops[k]
+    return parts
+
+
 def make_workload(w, seed):
     d, l, ar, t = gen.make_bta(w["n"], w["b"], w["a"], seed=seed, shift=w["shift"])
     r = gen.make_rhs(w["n"], w["b"], w["a"], NRHS, seed=seed + 1000)
@@ -353,14 +381,26 @@ def roofline_of(stats, prec, fp64_peak, peaks):
     return base
 
 
-def run_modes(args, bta, lib, step, W, ld_out, base_ms, dev, ref_inputs):
+def blockerr(x, y):
+    """Largest per-block relative Frobenius error of x against y (torch tensors)."""
+    import torch
+    if x.numel() == 0:
+        return 0.0
+    if x.dim() == 3:
+        num = torch.linalg.norm((x - y).flatten(1), dim=1)
+        den = torch.linalg.norm(y.flatten(1), dim=1).clamp_min(1e-300)
+        return float((num / den).max())
+    return float(torch.linalg.norm(x - y) / torch.linalg.norm(y).clamp_min(1e-300))
+
+
+def run_modes(args, bta, lib, step, W, ld_out, base_ms, dev, ref_inputs, base_phases):
     """Time the other precision modes on the same matrix; state each one's error
     against the main mode's result (per block, relative Frobenius) and its speedup."""
     import torch
     ref = [x.clone() for x in W]
     ref_ld = float(ld_out.item())
     res = {}
-    for mode in [m for m in args.modes.split(",") if m and m != args.precision]:
+    for mode in [m for m in (args.modes or "").split(",") if m and m != args.precision]:
         bta.set_precision(mode)
         for _ in range(args.warmup):
             step()
@@ -411,6 +451,36 @@ def run_modes(args, bta, lib, step, W, ld_out, base_ms, dev, ref_inputs):
                      "dtype": PREC_DTYPE[mode],
                      "roofline": roofline_of(stats, mode, 1.0, peaks),
                      "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()}}
+    # Partitioned form (the paper's P-way scheme on one device): factor + logdet + selinv.
+    for spec in [x for x in (args.partitioned or "").split(",") if x]:
+        prec, P = spec.split(":")
+        P = int(P)
+        bta.set_precision(prec)
+
+        def pstep():
+            for dst, src in zip(W, ref_inputs):
+                dst.copy_(src, non_blocking=True)
+            bta.factor_selinv_partitioned(W[0], W[1], W[2], W[3], parts=P, lb=1.8, logdet_out=ld_out)
+
+        for _ in range(args.warmup):
+            pstep()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            pstep()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        errs = {nm: blockerr(W[i], ref[i]) for i, nm in enumerate(["X_diag", "X_lower", "X_arrow", "X_tip"])}
+        errs["logdet"] = abs(float(ld_out.item()) - ref_ld) / abs(ref_ld)
+        base_fls = base_phases["factor"] + base_phases["logdet"] + base_phases["selinv"]
+        res[f"partitioned_{prec}_P{P}"] = {
+            "ms_per_matrix_factor_logdet_selinv": round(ms, 3),
+            "speedup_vs_" + args.precision + "_factor_logdet_selinv": round(base_fls / ms, 3),
+            "max_block_rel_err_vs_" + args.precision: {k: float(f"{v:.3e}") for k, v in errs.items()},
+            "parts": P, "load_balance_top": 1.8}
     return res
 
 
@@ -428,7 +498,7 @@ def run_ours(args, w, rank, world, local_rank):
     n, b, a = w["n"], w["b"], w["a"]
     bta.set_precision(args.precision)
 
-    arrays = make_workload(w, seed=rank)
+    arrays = make_workload(w, seed=rank_seed(rank))
     d, l, ar, t, r = arrays
     P = [torch.from_numpy(x).to(dev) for x in (d, l, ar, t, r)]
     W = [torch.empty_like(x) for x in P]
@@ -468,11 +538,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_per_step = ms / args.steps
     value = ms_per_step / world  # whole job: `world` matrices per step
 
@@ -505,11 +571,7 @@ def run_ours(args, w, rank, world, local_rank):
         e1.record()
         torch.cuda.synchronize(dev)
         barrier()
-        ms2 = e0.elapsed_time(e1)
-        if dist is not None:
-            tt = torch.tensor([ms2], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms2 = float(tt.item())
+        ms2 = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         h2d = sum(x.numel() * 8 for x in H)
         d2h = sum(x.numel() * 8 for x in O) + 8
         e2e = {"value": round(ms2 / k2 / world, 3), "unit": "ms/matrix", "h2d_bytes_per_step": h2d,
@@ -518,9 +580,6 @@ def run_ours(args, w, rank, world, local_rank):
 
     F = flops_factor(n, b, a) + flops_selinv(n, b, a)
     modes = {}
-    if rank == 0 and args.modes:
-        modes = run_modes(args, bta, lib, step, W, ld_out, ms_per_step, dev, P)
-        bta.set_precision(args.precision)
     out = None
     if rank == 0:
         # Kernel-level measurement pass (after the timed steps): per-launch events
@@ -560,6 +619,9 @@ def run_ours(args, w, rank, world, local_rank):
         e1.record()
         torch.cuda.synchronize(dev)
         peak_tf = pf.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        if args.modes or args.partitioned:
+            modes = run_modes(args, bta, lib, step, W, ld_out, ms_per_step, dev, P, phases)
+            bta.set_precision(args.precision)
 
         total_kernel_ms = sum(v[0] for v in stats.values())
         launches_per_step = sum(v[2] for v in stats.values())
@@ -606,6 +668,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "ozaki", "bf16x3"], default="fp64")
     ap.add_argument("--modes", default="ozaki,bf16x3",
                     help="other precision modes timed on the same matrix ('' to skip)")
+    ap.add_argument("--partitioned", default="ozaki:4,ozaki:8,fp64:4",
+                    help="partitioned runs 'precision:P,...' timed on the same matrix ('' to skip)")
     ap.add_argument("--cpu-target-s", type=float, default=10.0)
     ap.add_argument("--ref-target-s", type=float, default=5.0)
     args = ap.parse_args()

@@ -186,6 +186,29 @@ size_t bta_batch_workspace_bytes(int64_t n, int64_t b, int64_t a, int prec);
 int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int nstreams,
                               bta_stream_t stream);
 
+/* ---- Partitioned form (the paper's Sections 3.1-3.4 on one device) ------- */
+
+/*
+ * bta_factor_selinv_partitioned -- selected inversion (and log-det) of one BTA
+ * matrix by the partitioned scheme: the block rows are split into P partitions
+ * (top partition lb times a middle one; middle partitions >= 2 blocks), whose
+ * interior eliminations run concurrently on library streams (PPOBTAF,
+ * Algorithms 3-4: the middle partitions' shifting permutation with its fill-in),
+ * the 2P-1-block reduced system of the boundary blocks is factored and inverted
+ * (POBTARSSI, Section 3.3), and the partitions' interior blocks of X follow in
+ * concurrent backward sweeps (PPOBTASI, Algorithms 5-6). In place: A -> X, the
+ * same output as bta_factor followed by bta_selinv; the intermediate factor is of
+ * the permuted matrix, so no L is returned. logdet_out (device double, may be
+ * NULL) receives log det A. The large products follow bta_set_precision.
+ * ws: >= bta_partitioned_workspace_bytes(n, b, a, P, lb) bytes, 256-byte aligned.
+ * P is reduced when n is too small for it (P = 1 is the sequential method).
+ */
+size_t bta_partitioned_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t P, double lb);
+int bta_factor_selinv_partitioned(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                                  double* arrow, double* tip, int64_t P, double lb,
+                                  double* logdet_out, void* ws, size_t ws_bytes,
+                                  bta_stream_t stream);
+
 /* ---- Differentiation support ------------------------------------------- */
 
 /*
@@ -250,9 +273,10 @@ int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const doub
              double* C, int64_t ldc, void* ws, size_t ws_bytes, bta_stream_t stream);
 
 /*
- * bta_tc_status -- reads and clears the tensor-core kernels' timeout flag
- * (1: a bounded wait inside a tcgen05 kernel gave up and its tile was not
- * written; 0: none since the last read). Synchronous.
+ * bta_tc_status -- reads and clears the timeout flag of the library's bounded
+ * waits (the tcgen05 pipelines' mbarriers and the cooperative POTRF's grid
+ * barrier): 1 if any wait gave up since the last read (its results are then not
+ * valid), else 0. Synchronous.
  */
 int bta_tc_status(int* timed_out);
 

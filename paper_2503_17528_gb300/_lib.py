@@ -34,6 +34,9 @@ _SIGS = {
     "bta_probe_fp64_peak": [_p, _i64, ctypes.POINTER(ctypes.c_double), _p],
     "bta_batch_workspace_bytes": [_i64, _i64, _i64, ctypes.c_int],
     "bta_factor_selinv_batched": [_i64, ctypes.c_void_p, ctypes.c_int, _p],
+    "bta_partitioned_workspace_bytes": [_i64, _i64, _i64, _i64, ctypes.c_double],
+    "bta_factor_selinv_partitioned": [_i64, _i64, _i64, _p, _p, _p, _p, _i64, ctypes.c_double, _p, _p,
+                                      _sz, _p],
     "bta_grad_blocks": [_i64, _i64, _i64, _p, _p, _p, _p, _p, ctypes.c_double, ctypes.c_double,
                         _p, _p, _p, _p, _p, _p],
     "bta_dot": [_i64, _p, _p, _p, _p, _sz, _p],

@@ -176,3 +176,22 @@ def tc_status() -> int:
     v = ctypes.c_int(0)
     _check(_lib.load().bta_tc_status(ctypes.byref(v)), "bta_tc_status")
     return int(v.value)
+
+
+def factor_selinv_partitioned(diag, lower, arrow, tip, parts=4, lb=1.8, logdet_out=None):
+    """In place A -> X by the partitioned scheme (P concurrent partitions plus a
+    reduced system); returns log det A as a 0-d CUDA tensor."""
+    n, b, a = _dims(diag, lower, arrow, tip)
+    lib = _lib.load()
+    if logdet_out is None:
+        logdet_out = torch.empty((), dtype=torch.float64, device=diag.device)
+    with torch.cuda.device(diag.device):
+        nbytes = int(lib.bta_partitioned_workspace_bytes(n, b, a, parts, lb))
+        if nbytes == 0:
+            raise BTAError("bta_partitioned_workspace_bytes: invalid arguments")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=diag.device)
+        wp = ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+        _check(lib.bta_factor_selinv_partitioned(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                                 parts, lb, _ptr(logdet_out), wp, nbytes,
+                                                 _stream(diag.device)), "bta_factor_selinv_partitioned")
+    return logdet_out

@@ -37,7 +37,7 @@ struct Carver {
   }
 };
 
-struct FactorWs { double *Linv, *W, *Wa; void* tc; size_t tc_bytes; };
+struct FactorWs { double *Linv, *W, *Wa; void* coop; void* tc; size_t tc_bytes; };
 struct SelinvWs { double *Linv, *G, *H, *LtInv; void* tc; size_t tc_bytes; };
 
 extern int g_prec;
@@ -52,6 +52,7 @@ size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o, int prec
   w.Linv = c.take((size_t)(b * b));
   w.W = c.take((size_t)(b * b));
   w.Wa = c.take((size_t)(a * b + 1));
+  w.coop = (void*)c.take(kCoopScratch / sizeof(double));
   w.tc_bytes = tc_bytes_for(b, a, 1, prec);
   w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
   if (o) *o = w;
@@ -146,9 +147,16 @@ struct TcWs {
 // FP64 DMMA kernels run it.
 cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaStream_t s) {
   if (prec == BTA_PREC_FP64 || !routes_to_tc(prec, cls) || !tw.p) return gemm_f64(g, s);
-  int kmax = 0;
-  for (int i = 0; i < g.nterms; ++i) kmax = g.t[i].K > kmax ? g.t[i].K : kmax;
-  if (g.M >= 64 && g.N >= 64 && kmax >= 64) return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s);
+  int kmax = 0, ksum = 0;
+  for (int i = 0; i < g.nterms; ++i) {
+    kmax = g.t[i].K > kmax ? g.t[i].K : kmax;
+    ksum += g.t[i].K;
+  }
+  // The tensor-core path costs three launches and a splitting pass; it pays for
+  // products of at least 2^25 multiply-adds (a 512^3 block product).
+  const double macs = (double)g.M * g.N * ksum * g.nb1 * g.nb2;
+  if (g.M >= 64 && g.N >= 64 && kmax >= 64 && macs >= 33554432.0)
+    return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s);
   return gemm_f64(g, s);
 }
 
@@ -161,8 +169,13 @@ cudaError_t trtri_hook(const GemmArgs& g, void* ctx, cudaStream_t s) {
   return gemm_run(g, CLS_TRSM, ((HookCtx*)ctx)->tw, ((HookCtx*)ctx)->prec, s);
 }
 
+// Blocks of at least this order are factored by the single-launch cooperative
+// POTRF (one matrix at a time); smaller ones, and matrices of a batch running on
+// concurrent streams, use the panel-by-panel launches.
+constexpr int64_t kCoopMinB = 128;
+
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
-                double* tip, const FactorWs& w, int prec, cudaStream_t s) {
+                double* tip, const FactorWs& w, int prec, cudaStream_t s, bool coop = true) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b;
   TcWs tw;
@@ -170,7 +183,10 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   tw.bytes = w.tc_bytes;
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
-    BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+    if (coop && b >= kCoopMinB)
+      BTA_TRY(potrf_coop(Di, b, B, i * b, w.coop, s));
+    else
+      BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
     HookCtx hc{tw, prec};
     BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
     if (i + 1 < n) {
@@ -370,6 +386,338 @@ double entry_flops(int64_t n, int64_t b, int64_t a) {
   return (double)n * (7.0 * B * B * B + 6.0 * A * B * B);
 }
 
+
+// ---------------------------------------------------------------------------
+// Partitioned factorization and selected inversion on one device (the paper's
+// Sections 3.1-3.4). The block rows are split into P contiguous partitions: a
+// top one and P-1 middle ones. Eliminating the interior blocks of every
+// partition is a Schur complement onto the boundary blocks (the top partition's
+// last block, each middle partition's first and last block) and the tip, and the
+// partitions' eliminations are independent, so each runs on its own stream. In
+// a middle partition the first block s is ordered after the interior (the
+// paper's shifting permutation, never materialized): eliminating interior block
+// i couples s with i+1, a fill-in block carried as the coupling F = A~_{i+1,s}
+// and the factor column L_{s,i} (stored per interior block). The boundary blocks
+// form a BTA matrix with 2P-1 diagonal blocks (the reduced system), factored and
+// inverted as usual. Each partition's interior blocks of X then follow from
+// X L = L^{-T} on the permuted factor:
+//   X_{i+1,i} = -X_{i+1,i+1} G_i - X_{i+1,s} Gs_i - X_{n,i+1}^T H_i
+//   X_{i,s}   = -G_i^T X_{i+1,s} - Gs_i^T X_{s,s} - H_i^T X_{n,s}
+//   X_{n,i}   = -X_{n,i+1} G_i - X_{n,s} Gs_i - X_nn H_i
+//   X_{i,i}   =  M_i - X_{i+1,i}^T G_i - X_{i,s} Gs_i - X_{n,i}^T H_i
+// with G_i = L_{i+1,i} L_ii^{-1}, Gs_i = L_{s,i} L_ii^{-1}, H_i = L_{n,i} L_ii^{-1},
+// M_i = L_ii^{-T} L_ii^{-1} (the Gs terms vanish in the top partition).
+// ---------------------------------------------------------------------------
+constexpr int kMaxParts = 64;
+
+struct PartPlan {
+  int P = 0;
+  int64_t s[kMaxParts], e[kMaxParts];
+};
+
+// Sizes: the top partition is `lb` times a middle one (the paper's load-balancing
+// ratio; middle partitions carry the fill-in work), middle partitions >= 2 blocks.
+PartPlan plan_partitions(int64_t n, int P, double lb) {
+  PartPlan p;
+  if (P < 1) P = 1;
+  while (P > 1 && (double)n < lb + 2.0 * (P - 1)) --P;
+  if (P == 1) {
+    p.P = 1; p.s[0] = 0; p.e[0] = n;
+    return p;
+  }
+  int64_t m = (int64_t)((double)n / (lb + (P - 1)));
+  if (m < 2) m = 2;
+  int64_t top = n - m * (P - 1);
+  if (top < 1) { top = 1; m = (n - 1) / (P - 1); }
+  p.P = P;
+  p.s[0] = 0; p.e[0] = top;
+  int64_t at = top;
+  for (int j = 1; j < P; ++j) {
+    const int64_t len = (j == P - 1) ? n - at : m;
+    p.s[j] = at; p.e[j] = at + len;
+    at += len;
+  }
+  return p;
+}
+
+struct PartWs {
+  double *W, *Wa, *Ft, *LinvF, *U, *Ls, *Li, *G, *Gs, *H;
+  void* tc;
+  size_t tc_bytes;
+};
+
+struct PartLayout {
+  PartPlan plan;
+  PartWs part[kMaxParts];
+  double *rd, *rl, *ra, *rt, *ldp, *rldp;
+  FactorWs rf;
+  SelinvWs rs;
+  int64_t nr;
+};
+
+size_t part_layout(int64_t n, int64_t b, int64_t a, int P, double lb, int prec, void* base,
+                   PartLayout* out) {
+  Carver c(base);
+  PartLayout L;
+  L.plan = plan_partitions(n, P, lb);
+  const int64_t bb = b * b;
+  for (int j = 0; j < L.plan.P; ++j) {
+    const int64_t nj = L.plan.e[j] - L.plan.s[j];
+    PartWs& w = L.part[j];
+    w.W = c.take(bb);
+    w.Wa = c.take(a * b + 1);
+    w.Ft = c.take(bb);
+    w.LinvF = c.take(bb);
+    w.U = c.take(a * a + 1);
+    w.Ls = c.take(j ? nj * bb : 1);
+    w.Li = c.take(nj * bb);
+    w.G = c.take(nj * bb);
+    w.Gs = c.take(j ? nj * bb : 1);
+    w.H = c.take(nj * a * b + 1);
+    w.tc_bytes = tc_bytes_for(b, a, nj, prec);
+    w.tc = w.tc_bytes ? (void*)c.take(w.tc_bytes / sizeof(double) + 1) : nullptr;
+  }
+  L.nr = 2 * L.plan.P - 1;
+  L.rd = c.take(L.nr * bb);
+  L.rl = c.take((L.nr - 1) * bb + 1);
+  L.ra = c.take(L.nr * a * b + 1);
+  L.rt = c.take(a * a + 1);
+  L.ldp = c.take(n + 1);
+  L.rldp = c.take(L.nr + 2);
+  const size_t fsz = factor_ws(L.nr, b, a, base ? (char*)base + c.off : nullptr, &L.rf, prec);
+  c.off += align_up(fsz);
+  const size_t ssz = selinv_ws(L.nr, b, a, base ? (char*)base + c.off : nullptr, &L.rs, prec);
+  c.off += align_up(ssz);
+  if (out) *out = L;
+  return c.off;
+}
+
+// One interior elimination step of block i in partition storage: L_ii, L_{i+1,i},
+// L_{n,i}, the Schur updates of block i+1 and of the arrow, and the tip part into U.
+int part_eliminate(int64_t i, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                   const PartWs& w, int prec, cudaStream_t s) {
+  const int B = (int)b, Aa = (int)a;
+  const int64_t bb = b * b;
+  TcWs tw;
+  tw.p = w.tc;
+  tw.bytes = w.tc_bytes;
+  double* Di = diag + i * bb;
+  BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+  HookCtx hc{tw, prec};
+  BTA_TRY(trtri_blocks(Di, b, bb, w.LinvF, b, bb, 1, B, s, trtri_hook, &hc));
+  double* Li = lower + i * bb;
+  BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, w.LinvF, b, OP_T, TRI_UPPER, B, 1.0), w.W, b,
+                            B, B, 0.0, 0), CLS_TRSM, tw, prec, s));
+  BTA_TRY(cudaMemcpyAsync(Li, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0), Di + bb, b,
+                            B, B, 1.0, 1), CLS_SCHUR, tw, prec, s));
+  if (a > 0) {
+    double* Ai = arrow + i * a * b;
+    BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, w.LinvF, b, OP_T, TRI_UPPER, B, 1.0), w.Wa,
+                              b, Aa, B, 0.0, 0), CLS_TRSM, tw, prec, s));
+    BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0), Ai + a * b,
+                              b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
+    BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0), w.U, a, Aa,
+                              Aa, 1.0, 1), CLS_SCHUR, tw, prec, s));
+  }
+  return 0;
+}
+
+int part_factor(int j, const PartLayout& L, int64_t b, int64_t a, double* diag, double* lower,
+                double* arrow, int prec, cudaStream_t s) {
+  const PartWs& w = L.part[j];
+  const int64_t st = L.plan.s[j], en = L.plan.e[j], bb = b * b;
+  const int B = (int)b, Aa = (int)a;
+  TcWs tw;
+  tw.p = w.tc;
+  tw.bytes = w.tc_bytes;
+  if (a > 0) BTA_TRY(cudaMemsetAsync(w.U, 0, a * a * sizeof(double), s));
+  if (j == 0) {
+    for (int64_t i = st; i < en - 1; ++i) {
+      int rc = part_eliminate(i, b, a, diag, lower, arrow, w, prec, s);
+      if (rc) return rc;
+    }
+    if (en - 1 > st) BTA_TRY(logdet_partials(diag + st * bb, en - 1 - st, b, nullptr, 0, L.ldp + st, s));
+    return 0;
+  }
+  // Middle partition: the coupling (first interior, s) is A_{s+1,s}.
+  BTA_TRY(cudaMemcpyAsync(w.Ft, lower + st * bb, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double* Ds = diag + st * bb;
+  double* As = arrow + st * a * b;
+  for (int64_t i = st + 1; i < en - 1; ++i) {
+    int rc = part_eliminate(i, b, a, diag, lower, arrow, w, prec, s);
+    if (rc) return rc;
+    // (part_eliminate left L_ii^{-1} in LinvF)
+    double* Lsi = w.Ls + (i - st - 1) * bb;
+    double* Lo = lower + i * bb;
+    // L_{s,i} = F^T L_ii^{-T}
+    BTA_TRY(gemm_run(one_term(term(w.Ft, b, OP_T, TRI_NONE, w.LinvF, b, OP_T, TRI_UPPER, B, 1.0), Lsi,
+                              b, B, B, 0.0, 0), CLS_TRSM, tw, prec, s));
+    // A_ss -= L_{s,i} L_{s,i}^T ; F <- -L_{i+1,i} L_{s,i}^T ; A_{n,s} -= L_{n,i} L_{s,i}^T
+    BTA_TRY(gemm_run(one_term(term(Lsi, b, OP_N, TRI_NONE, Lsi, b, OP_T, TRI_NONE, B, -1.0), Ds, b, B,
+                              B, 1.0, 1), CLS_SCHUR, tw, prec, s));
+    BTA_TRY(gemm_run(one_term(term(Lo, b, OP_N, TRI_NONE, Lsi, b, OP_T, TRI_NONE, B, -1.0), w.Ft, b, B,
+                              B, 0.0, 0), CLS_SCHUR, tw, prec, s));
+    if (a > 0)
+      BTA_TRY(gemm_run(one_term(term(arrow + i * a * b, b, OP_N, TRI_NONE, Lsi, b, OP_T, TRI_NONE, B,
+                                     -1.0), As, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
+  }
+  if (en - 1 > st + 1)
+    BTA_TRY(logdet_partials(diag + (st + 1) * bb, en - 2 - st, b, nullptr, 0, L.ldp + st + 1, s));
+  return 0;
+}
+
+int part_sweep(int j, const PartLayout& L, int64_t b, int64_t a, double* diag, double* lower,
+               double* arrow, const double* tip, int prec, cudaStream_t s) {
+  const PartWs& w = L.part[j];
+  const int64_t st = L.plan.s[j], en = L.plan.e[j], bb = b * b, ab = a * b;
+  const int B = (int)b, Aa = (int)a;
+  const int64_t i0 = j == 0 ? st : st + 1, i1 = en - 1, m = i1 - i0;
+  TcWs tw;
+  tw.p = w.tc;
+  tw.bytes = w.tc_bytes;
+  if (m > 0) {
+    HookCtx hc{tw, prec};
+    BTA_TRY(trtri_blocks(diag + i0 * bb, b, bb, w.Li, b, bb, (int)m, B, s, trtri_hook, &hc));
+    GemmArgs g = one_term(term(lower + i0 * bb, b, OP_N, TRI_NONE, w.Li, b, OP_N, TRI_LOWER, B, 1.0),
+                          w.G, b, B, B, 0.0, 0);
+    g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)m;
+    BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
+    if (j > 0) {
+      GemmArgs gs = one_term(term(w.Ls, b, OP_N, TRI_NONE, w.Li, b, OP_N, TRI_LOWER, B, 1.0), w.Gs, b,
+                             B, B, 0.0, 0);
+      gs.t[0].sA1 = bb; gs.t[0].sB1 = bb; gs.sC1 = bb; gs.nb1 = (int)m;
+      BTA_TRY(gemm_run(gs, CLS_SELINV, tw, prec, s));
+    }
+    if (a > 0) {
+      GemmArgs gh = one_term(term(arrow + i0 * ab, b, OP_N, TRI_NONE, w.Li, b, OP_N, TRI_LOWER, B,
+                                  1.0), w.H, b, Aa, B, 0.0, 0);
+      gh.t[0].sA1 = ab; gh.t[0].sB1 = bb; gh.sC1 = ab; gh.nb1 = (int)m;
+      BTA_TRY(gemm_run(gh, CLS_SELINV, tw, prec, s));
+    }
+    GemmArgs gm = one_term(term(w.Li, b, OP_T, TRI_UPPER, w.Li, b, OP_N, TRI_LOWER, B, 1.0),
+                           diag + i0 * bb, b, B, B, 0.0, 1);
+    gm.t[0].sA1 = bb; gm.t[0].sB1 = bb; gm.sC1 = bb; gm.nb1 = (int)m;
+    BTA_TRY(gemm_run(gm, CLS_SELINV, tw, prec, s));
+  }
+  double* Ds = diag + st * bb;   // X_ss (middle partitions)
+  double* As = arrow + st * ab;  // X_{n,s}
+  for (int64_t i = i1 - 1; i >= i0; --i) {
+    const int64_t k = i - i0;
+    const double* Gk = w.G + k * bb;
+    const double* Gsk = w.Gs + k * bb;
+    const double* Hk = w.H + k * ab;
+    double* Di = diag + i * bb;
+    // X_{i+1,i}
+    GemmArgs g1 = one_term(term(Di + bb, b, OP_N, TRI_NONE, Gk, b, OP_N, TRI_NONE, B, -1.0),
+                           lower + i * bb, b, B, B, 0.0, 0);
+    if (j > 0) g1.t[g1.nterms++] = term(w.Ft, b, OP_N, TRI_NONE, Gsk, b, OP_N, TRI_NONE, B, -1.0);
+    if (a > 0) g1.t[g1.nterms++] = term(arrow + (i + 1) * ab, b, OP_T, TRI_NONE, Hk, b, OP_N, TRI_NONE, Aa, -1.0);
+    BTA_TRY(gemm_run(g1, CLS_SELINV, tw, prec, s));
+    // X_{i,s} (middle) into W
+    if (j > 0) {
+      GemmArgs g2 = one_term(term(Gk, b, OP_T, TRI_NONE, w.Ft, b, OP_N, TRI_NONE, B, -1.0), w.W, b, B,
+                             B, 0.0, 0);
+      g2.t[g2.nterms++] = term(Gsk, b, OP_T, TRI_NONE, Ds, b, OP_N, TRI_NONE, B, -1.0);
+      if (a > 0) g2.t[g2.nterms++] = term(Hk, b, OP_T, TRI_NONE, As, b, OP_N, TRI_NONE, Aa, -1.0);
+      BTA_TRY(gemm_run(g2, CLS_SELINV, tw, prec, s));
+    }
+    // X_{n,i}
+    if (a > 0) {
+      GemmArgs g3 = one_term(term(tip, a, OP_N, TRI_NONE, Hk, b, OP_N, TRI_NONE, Aa, -1.0),
+                             arrow + i * ab, b, Aa, B, 0.0, 0);
+      g3.t[g3.nterms++] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gk, b, OP_N, TRI_NONE, B, -1.0);
+      if (j > 0) g3.t[g3.nterms++] = term(As, b, OP_N, TRI_NONE, Gsk, b, OP_N, TRI_NONE, B, -1.0);
+      BTA_TRY(gemm_run(g3, CLS_SELINV, tw, prec, s));
+    }
+    // X_ii (lower tiles, then mirrored)
+    GemmArgs g4{};
+    g4.C = Di; g4.ldc = b; g4.M = B; g4.N = B; g4.beta = 1.0; g4.lowerC = 1; g4.nb1 = 1; g4.nb2 = 1;
+    g4.t[g4.nterms++] = term(lower + i * bb, b, OP_T, TRI_NONE, Gk, b, OP_N, TRI_NONE, B, -1.0);
+    if (j > 0) g4.t[g4.nterms++] = term(w.W, b, OP_N, TRI_NONE, Gsk, b, OP_N, TRI_NONE, B, -1.0);
+    if (a > 0) g4.t[g4.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hk, b, OP_N, TRI_NONE, Aa, -1.0);
+    BTA_TRY(gemm_run(g4, CLS_SELINV, tw, prec, s));
+    BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
+    if (j > 0) BTA_TRY(cudaMemcpyAsync(w.Ft, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (j > 0) BTA_TRY(cudaMemcpyAsync(lower + st * bb, w.Ft, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return 0;
+}
+
+int partitioned_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
+                     double* tip, double* logdet_out, const PartLayout& L, int prec, cudaStream_t s0) {
+  const PartPlan& pl = L.plan;
+  const int P = pl.P;
+  const int64_t bb = b * b, ab = a * b;
+  StreamPool* pool = nullptr;
+  BTA_TRY(pool_for(P, &pool));
+  BTA_TRY(cudaMemsetAsync(L.ldp, 0, (n + 1) * sizeof(double), s0));
+  auto fork = [&]() -> int {
+    BTA_TRY(cudaEventRecord(pool->fork, s0));
+    for (int j = 0; j < P; ++j) BTA_TRY(cudaStreamWaitEvent(pool->streams[j], pool->fork, 0));
+    return 0;
+  };
+  auto join = [&]() -> int {
+    for (int j = 0; j < P; ++j) {
+      BTA_TRY(cudaEventRecord(pool->join[j], pool->streams[j]));
+      BTA_TRY(cudaStreamWaitEvent(s0, pool->join[j], 0));
+    }
+    return 0;
+  };
+  int rc = fork();
+  if (rc) return rc;
+  for (int j = 0; j < P; ++j) {
+    rc = part_factor(j, L, b, a, diag, lower, arrow, prec, pool->streams[j]);
+    if (rc) return rc;
+  }
+  rc = join();
+  if (rc) return rc;
+  // Reduced system: [last_0, first_1, last_1, ..., first_{P-1}, last_{P-1}].
+  int64_t idx[2 * kMaxParts];
+  int64_t nr = 0;
+  idx[nr++] = pl.e[0] - 1;
+  for (int j = 1; j < P; ++j) {
+    idx[nr++] = pl.s[j];
+    idx[nr++] = pl.e[j] - 1;
+  }
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  for (int64_t k = 0; k < nr; ++k) {
+    BTA_TRY(cudaMemcpyAsync(L.rd + k * bb, diag + idx[k] * bb, bb * 8, dd, s0));
+    if (a > 0) BTA_TRY(cudaMemcpyAsync(L.ra + k * ab, arrow + idx[k] * ab, ab * 8, dd, s0));
+  }
+  for (int j = 1; j < P; ++j) {
+    BTA_TRY(cudaMemcpyAsync(L.rl + (2 * j - 2) * bb, lower + (pl.s[j] - 1) * bb, bb * 8, dd, s0));
+    BTA_TRY(cudaMemcpyAsync(L.rl + (2 * j - 1) * bb, L.part[j].Ft, bb * 8, dd, s0));
+  }
+  if (a > 0) {
+    BTA_TRY(cudaMemcpyAsync(L.rt, tip, a * a * 8, dd, s0));
+    for (int j = 0; j < P; ++j) BTA_TRY(axpy_f64(a * a, 1.0, L.part[j].U, L.rt, s0));
+  }
+  rc = factor_impl(nr, b, a, L.rd, L.rl, L.ra, L.rt, L.rf, prec, s0);
+  if (rc) return rc;
+  BTA_TRY(logdet_partials(L.rd, nr, b, L.rt, a, L.rldp, s0));
+  if (logdet_out) BTA_TRY(logdet_combine(L.ldp, n, L.rldp, nr + (a > 0 ? 1 : 0), logdet_out, s0));
+  rc = selinv_impl(nr, b, a, L.rd, L.rl, L.ra, L.rt, L.rs, prec, s0);
+  if (rc) return rc;
+  for (int64_t k = 0; k < nr; ++k) {
+    BTA_TRY(cudaMemcpyAsync(diag + idx[k] * bb, L.rd + k * bb, bb * 8, dd, s0));
+    if (a > 0) BTA_TRY(cudaMemcpyAsync(arrow + idx[k] * ab, L.ra + k * ab, ab * 8, dd, s0));
+  }
+  for (int j = 1; j < P; ++j) {
+    BTA_TRY(cudaMemcpyAsync(lower + (pl.s[j] - 1) * bb, L.rl + (2 * j - 2) * bb, bb * 8, dd, s0));
+    BTA_TRY(cudaMemcpyAsync(L.part[j].Ft, L.rl + (2 * j - 1) * bb, bb * 8, dd, s0));
+  }
+  if (a > 0) BTA_TRY(cudaMemcpyAsync(tip, L.rt, a * a * 8, dd, s0));
+  rc = fork();
+  if (rc) return rc;
+  for (int j = 0; j < P; ++j) {
+    rc = part_sweep(j, L, b, a, diag, lower, arrow, tip, prec, pool->streams[j]);
+    if (rc) return rc;
+  }
+  return join();
+}
+
 }  // namespace
 
 extern "C" {
@@ -535,7 +883,7 @@ int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int
     cudaStream_t st = pool->streams[j];
     FactorWs fw;
     factor_ws(e.n, e.b, e.a, e.ws, &fw, e.prec);
-    int rc = factor_impl(e.n, e.b, e.a, e.diag, e.lower, e.arrow, e.tip, fw, e.prec, st);
+    int rc = factor_impl(e.n, e.b, e.a, e.diag, e.lower, e.arrow, e.tip, fw, e.prec, st, false);
     if (rc) return rc;
     if (e.logdet_out) {
       LogdetWs lw;
@@ -552,6 +900,29 @@ int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int
     BTA_TRY(cudaStreamWaitEvent(s0, pool->join[i], 0));
   }
   return 0;
+}
+
+size_t bta_partitioned_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t P, double lb) {
+  if (check_sizes(n, b, a) || P < 1 || P > kMaxParts || !(lb > 0.0)) return 0;
+  return part_layout(n, b, a, (int)P, lb, g_prec, nullptr, nullptr);
+}
+
+int bta_factor_selinv_partitioned(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                                  double* arrow, double* tip, int64_t P, double lb,
+                                  double* logdet_out, void* ws, size_t ws_bytes,
+                                  bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  if (P < 1 || P > kMaxParts) return -8;
+  if (!(lb > 0.0)) return -9;
+  if (logdet_out && misaligned(logdet_out)) return -10;
+  const int prec = g_prec;
+  PartLayout L;
+  const size_t need = part_layout(n, b, a, (int)P, lb, prec, ws, &L);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -11;
+  if (ws_bytes < need) return -12;
+  return partitioned_impl(n, b, a, diag, lower, arrow, tip, logdet_out, L, prec, (cudaStream_t)stream);
 }
 
 int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,
@@ -641,7 +1012,10 @@ int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const doub
 
 int bta_tc_status(int* timed_out) {
   if (!timed_out) return -1;
-  BTA_TRY(tc_error_read_reset(timed_out));
+  int a = 0, b = 0;
+  BTA_TRY(tc_error_read_reset(&a));
+  BTA_TRY(wait_error_read_reset(&b));
+  *timed_out = (a || b) ? 1 : 0;
   return 0;
 }
 

@@ -26,8 +26,9 @@ struct GemmTerm {
 };
 
 // C = beta * C + sum_t alpha_t op(A_t) op(B_t) over a 2-D batch (z1, z2).
+constexpr int kMaxTerms = 4;
 struct GemmArgs {
-  GemmTerm t[2];
+  GemmTerm t[kMaxTerms];
   int nterms;
   double* C;
   int64_t ldc, sC1, sC2;
@@ -56,6 +57,14 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s);
 cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          long long info_row0, long long info_rstride,
                          cudaStream_t s);
+// Cooperative single-launch POTRF of one nrow x nrow block (nrow >= 64 pays);
+// scratch: coop_scratch_bytes, 256-byte aligned.
+constexpr size_t kCoopScratch = 256 + 2 * T * T * sizeof(double);
+cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
+                       cudaStream_t s);
+// Reads and clears the timeout flag of the cooperative kernels' grid barriers.
+cudaError_t wait_error_read_reset(int* out);
+
 // Inverse of lower-triangular blocks: Linv (separate buffer, same layout) =
 // L^{-1}, strict upper triangle zero. The doubling products go through `hook`
 // when given (it may run them on the tensor cores), else the FP64 kernels.
@@ -71,6 +80,15 @@ cudaError_t mirror_lower(double* A, int64_t ld, int64_t sb, int count, int nrow,
 cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b,
                        const double* tip, int64_t a, double* partial,
                        double* out, cudaStream_t s);
+
+// Per-block log sums (partial[i] = sum_k log diag(block i); the tip last if a > 0).
+cudaError_t logdet_partials(const double* diag, int64_t n, int64_t b, const double* tip, int64_t a,
+                            double* partial, cudaStream_t s);
+// out = 2 * (sum p1 + sum p2), fixed order.
+cudaError_t logdet_combine(const double* p1, int64_t n1, const double* p2, int64_t n2, double* out,
+                           cudaStream_t s);
+// y += alpha x over n doubles.
+cudaError_t axpy_f64(int64_t n, double alpha, const double* x, double* y, cudaStream_t s);
 
 // Solve pieces (rhs row-major [rows][R]).
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x,

@@ -8,6 +8,8 @@
 // operands skip the k-range that is known to be zero.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "bta_internal.cuh"
@@ -449,6 +451,277 @@ __global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t 
 
 static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// ---------------------------------------------------------------------------
+// Cooperative POTRF of one block: the whole right-looking tile Cholesky in one
+// launch whose CTAs are all resident (cooperative launch), separated by
+// bounded grid barriers. Per step k:
+//   A. every CTA takes 8-row slices of the panel tiles (r, k), r > k:
+//      L(r,k) = A(r,k) L_kk^{-T} with the explicit L_kk^{-1} (DMMA);
+//   B. CTA 0 applies the step-k update to tile (k+1, k+1) first, factors it and
+//      inverts the factor (look-ahead: the next step's serial work), while the
+//      other CTAs apply the step-k updates to every other trailing tile.
+// The grid barrier counts arrivals and releases a generation word; a wait that
+// exceeds its poll limit records the timeout and lets the CTA go on, so the
+// kernel always ends (the caller reads the flag with bta_tc_status).
+// ---------------------------------------------------------------------------
+__device__ int g_wait_error;
+
+struct CoopBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+__device__ __forceinline__ void grid_barrier(CoopBar* bar, unsigned nblocks, unsigned& gen) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g0 = gen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned polls = 0;
+      while (atomicAdd(&bar->gen, 0u) == g0) {
+        if (++polls > (1u << 24)) {
+          atomicExch(&g_wait_error, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen = g0 + 1;
+  }
+  __syncthreads();
+}
+
+// Shared-memory Cholesky of a tb x tb tile in S (lower part valid); returns with
+// S = L (zero above) and rd[j] = 1 / L_jj. Records a failed pivot.
+__device__ void coop_factor(double (*S)[T + 1], double* rd, int tb, long long row_base) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < tb; ++j) {
+    if (tid == 0) {
+      double d = S[j][j];
+      if (!(d > 0.0)) {
+        record_failure(row_base + j + 1);
+        d = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      const double y = rsqrt_newton(d);
+      S[j][j] = d * y;
+      rd[j] = y;
+    }
+    __syncthreads();
+    const double r = rd[j];
+    for (int i = j + 1 + tid; i < tb; i += blockDim.x) S[i][j] *= r;
+    __syncthreads();
+    const int w = tb - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e / w, c = j + 1 + e % w;
+      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, c = e % T;
+    if (c > i) S[i][c] = 0.0;
+  }
+  __syncthreads();
+}
+
+// C(32 x 32, global) -= P Q^T with P, Q 32 x 32 tiles in shared memory; 8 warps,
+// each two 8 x 8 DMMA tiles of the output.
+__device__ __forceinline__ void coop_tile_update(double* C, int64_t ld, int rows, int cols,
+                                                 double (*P)[T + 1], double (*Q)[T + 1], int kb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int m0 = (warp >> 1) * 8, n0 = (warp & 1) * 16;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int ks = 0; ks < kb; ks += 4) {
+    const double a = P[m0 + gq][ks + tq];
+    dmma_8x8x4(acc[0], a, Q[n0 + gq][ks + tq]);
+    dmma_8x8x4(acc[1], a, Q[n0 + 8 + gq][ks + tq]);
+  }
+#pragma unroll
+  for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = m0 + gq, c = n0 + ni * 8 + 2 * tq + j;
+      if (r < rows && c < cols) C[(int64_t)r * ld + c] -= acc[ni][j];
+    }
+}
+
+struct CoopArgs {
+  double* A;
+  int64_t ld;
+  int nrow;
+  long long row0;
+  CoopBar* bar;
+  double* rdiag;  // [2][T] scratch: 1 / L_jj of the current diagonal tile (by step parity)
+};
+
+__global__ void __launch_bounds__(256) potrf_coop_kernel(CoopArgs p) {
+  __shared__ double S[T][T + 1];
+  __shared__ double P[T][T + 1];
+  __shared__ double Q[T][T + 1];
+  __shared__ double rd[T];
+  const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
+  const int nt = (p.nrow + T - 1) / T;
+  unsigned gen = 0;
+  double* A = p.A;
+  const int64_t ld = p.ld;
+
+  auto tb_of = [&](int t) { return min(T, p.nrow - t * T); };
+  // Step 0's diagonal tile.
+  if (bid == 0) {
+    const int tb = tb_of(0);
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      S[i][j] = (i < tb && j <= i) ? A[(int64_t)i * ld + j] : 0.0;
+    }
+    __syncthreads();
+    coop_factor(S, rd, tb, p.row0);
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      if (i < tb && j < tb) A[(int64_t)i * ld + j] = S[i][j];
+    }
+    if (tid < T) p.rdiag[tid] = rd[tid];
+  }
+  grid_barrier(p.bar, G, gen);
+  for (int k = 0; k < nt; ++k) {
+    const int o = k * T, tbk = tb_of(k);
+    const double* rdk = p.rdiag + (k & 1) * T;
+    // A. panel: 8-row slices of tiles r > k solve X L_kk^T = A(r,k) by a column sweep.
+    const int nslices = (nt - k - 1) * 4;
+    for (int sl = bid; sl < nslices; sl += G) {
+      const int r = k + 1 + sl / 4, rs = (sl % 4) * 8;
+      const int ro = r * T + rs, rows = min(8, p.nrow - ro);
+      __syncthreads();
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        Q[i][j] = (i < tbk && j <= i) ? A[(int64_t)(o + i) * ld + o + j] : 0.0;  // L_kk
+        if (i < 8) P[i][j] = (i < rows && j < tbk) ? A[(int64_t)(ro + i) * ld + o + j] : 0.0;
+      }
+      if (tid < T) rd[tid] = rdk[tid];
+      __syncthreads();
+      for (int j = 0; j < tbk; ++j) {
+        if (tid < rows) P[tid][j] *= rd[j];
+        __syncthreads();
+        const int w = tbk - j - 1;
+        for (int e = tid; e < rows * w; e += blockDim.x) {
+          const int i = e / w, c = j + 1 + e % w;
+          P[i][c] -= P[i][j] * Q[c][j];
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < rows * tbk; e += blockDim.x) {
+        const int i = e / tbk, c = e % tbk;
+        A[(int64_t)(ro + i) * ld + o + c] = P[i][c];
+      }
+    }
+    grid_barrier(p.bar, G, gen);
+    if (k + 1 == nt) break;
+    // B. trailing updates of step k; CTA 0 takes tile (k+1, k+1) and factors it.
+    const int nrest = nt - k - 1;                      // trailing tile rows/cols: k+1 .. nt-1
+    const long long ntiles = (long long)nrest * (nrest + 1) / 2;
+    if (bid == 0) {
+      const int o1 = o + T, tb1 = tb_of(k + 1);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        P[i][j] = (i < tb1 && j < tbk) ? A[(int64_t)(o1 + i) * ld + o + j] : 0.0;
+        S[i][j] = (i < tb1 && j <= i) ? A[(int64_t)(o1 + i) * ld + o1 + j] : 0.0;
+      }
+      __syncthreads();
+      // S -= P P^T (lower part), in shared memory
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (j <= i && i < tb1) {
+          double acc = 0.0;
+          for (int c = 0; c < tbk; ++c) acc = fma(P[i][c], P[j][c], acc);
+          S[i][j] -= acc;
+        }
+      }
+      __syncthreads();
+      coop_factor(S, rd, tb1, p.row0 + o1);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (i < tb1 && j < tb1) A[(int64_t)(o1 + i) * ld + o1 + j] = S[i][j];
+      }
+      if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
+    }
+    // Tiles of the trailing lower triangle other than (k+1, k+1), spread over CTAs 1..G-1
+    // (CTA 0 joins when G == 1).
+    const int workers = G > 1 ? G - 1 : 1, wid = G > 1 ? bid - 1 : 0;
+    if (G == 1 || bid > 0) {
+      for (long long t = 1 + wid; t < ntiles; t += workers) {
+        int rr = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(rr + 1) * (rr + 2) / 2 <= t) ++rr;
+        while ((long long)rr * (rr + 1) / 2 > t) --rr;
+        const int cc = (int)(t - (long long)rr * (rr + 1) / 2);
+        const int r = k + 1 + rr, c = k + 1 + cc;
+        const int rb = tb_of(r), cb = tb_of(c);
+        __syncthreads();
+        for (int e = tid; e < T * T; e += blockDim.x) {
+          const int i = e / T, j = e % T;
+          P[i][j] = (i < rb && j < tbk) ? A[(int64_t)(r * T + i) * ld + o + j] : 0.0;
+          Q[i][j] = (i < cb && j < tbk) ? A[(int64_t)(c * T + i) * ld + o + j] : 0.0;
+        }
+        __syncthreads();
+        coop_tile_update(A + (int64_t)(r * T) * ld + c * T, ld, rb, cb, P, Q, T);
+      }
+    }
+    grid_barrier(p.bar, G, gen);
+  }
+  // Strict upper triangle of the block -> 0.
+  for (long long e = (long long)bid * blockDim.x + tid; e < (long long)p.nrow * p.nrow;
+       e += (long long)G * blockDim.x) {
+    const int i = (int)(e / p.nrow), j = (int)(e % p.nrow);
+    if (j > i) A[(int64_t)i * ld + j] = 0.0;
+  }
+}
+
+static int coop_grid(int nt) {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, potrf_coop_kernel, 256, 0);
+    cached = per >= 1 ? sms : 0;  // one CTA per SM: the FP64 pipe is per SM, barriers stay cheap
+  }
+  (void)nt;
+  return cached;
+}
+
+cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
+                       cudaStream_t s) {
+  CoopArgs p;
+  p.A = A;
+  p.ld = ld;
+  p.nrow = nrow;
+  p.row0 = info_row0;
+  p.bar = (CoopBar*)scratch;
+  p.rdiag = (double*)((char*)scratch + 256);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(CoopBar), s);
+  if (e != cudaSuccess) return e;
+  const int G = coop_grid((nrow + T - 1) / T);
+  if (G < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {&p};
+  TimedLaunch tl(K_POTRF_TILE, 0.0, s);
+  return cudaLaunchCooperativeKernel((void*)potrf_coop_kernel, dim3(G), dim3(256), args, 0, s);
+}
+
+cudaError_t wait_error_read_reset(int* out) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_wait_error, sizeof(int));
+  if (e != cudaSuccess) return e;
+  *out = v;
+  const int zero = 0;
+  return cudaMemcpyToSymbol(g_wait_error, &zero, sizeof(int));
+}
+
+
+
 cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          long long info_row0, long long info_rstride, cudaStream_t s) {
   if (count <= 0 || nrow <= 0) return cudaSuccess;
@@ -582,6 +855,44 @@ __global__ void logdet_final_kernel(const double* partial, int64_t count, double
   }
 }
 
+cudaError_t logdet_partials(const double* diag, int64_t n, int64_t b, const double* tip, int64_t a,
+                            double* partial, cudaStream_t s) {
+  const int64_t count = n + (a > 0 ? 1 : 0);
+  if (count <= 0) return cudaSuccess;
+  TimedLaunch tl(K_LOGDET, 0.0, s);
+  logdet_partial_kernel<<<(unsigned)count, 256, 0, s>>>(diag, n, b, tip, a, partial);
+  return cudaGetLastError();
+}
+
+// out = 2 * (sum p1[0..n1) + sum p2[0..n2)), in that order.
+__global__ void logdet_combine_kernel(const double* p1, int64_t n1, const double* p2, int64_t n2,
+                                      double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int64_t z = 0; z < n1; ++z) s += p1[z];
+    for (int64_t z = 0; z < n2; ++z) s += p2[z];
+    *out = 2.0 * s;
+  }
+}
+
+cudaError_t logdet_combine(const double* p1, int64_t n1, const double* p2, int64_t n2, double* out,
+                           cudaStream_t s) {
+  logdet_combine_kernel<<<1, 32, 0, s>>>(p1, n1, p2, n2, out);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(int64_t n, double alpha, const double* x, double* y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += alpha * x[e];
+}
+
+cudaError_t axpy_f64(int64_t n, double alpha, const double* x, double* y, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  axpy_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1216), 256, 0, s>>>(n, alpha, x, y);
+  return cudaGetLastError();
+}
+
 cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b, const double* tip, int64_t a,
                        double* partial, double* out, cudaStream_t s) {
   const int64_t count = n + (a > 0 ? 1 : 0);
@@ -606,11 +917,22 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
 }
 
+constexpr int kTrsvPrefetch = 4;  // row tiles per CTA whose L tiles are prefetched into registers
+
+// L tile element for the update of row tile r by solved tile k: L(r,k) (forward)
+// or L(k,r)^T (transposed), as Lk[i][c] with i in tile r, c in tile k.
+__device__ __forceinline__ double trsv_tile_el(const double* L, int64_t ld, int trans, int ro, int rb,
+                                               int o, int tb, int i, int c) {
+  if (i >= rb || c >= tb) return 0.0;
+  return trans ? L[(int64_t)(o + c) * ld + ro + i] : L[(int64_t)(ro + i) * ld + o + c];
+}
+
 __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
                                                            double* x, int64_t ldx, int R,
                                                            int trans) {
   __shared__ double Xk[T][65];
   __shared__ double Lk[T][T + 1];
+  __shared__ double Ld[T][T + 1];
   __shared__ double rdiag[T];
   unsigned rank, csize;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
@@ -620,13 +942,36 @@ __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int6
   for (int step = 0; step < nt; ++step) {
     const int k = trans ? nt - 1 - step : step;
     const int o = k * T, tb = min(T, nrow - o);
-    if ((unsigned)(k % (int)csize) == rank) {
+    const bool owner = (unsigned)(k % (int)csize) == rank;
+    // This CTA's row tiles still to update: r_first + t * csize, t < count.
+    int r_first, count;
+    if (!trans) {
+      r_first = k + 1 + (int)((rank + csize - (unsigned)((k + 1) % (int)csize)) % csize);
+      count = r_first < nt ? (nt - 1 - r_first) / (int)csize + 1 : 0;
+    } else {
+      r_first = (int)rank;
+      count = r_first < k ? (k - 1 - r_first) / (int)csize + 1 : 0;
+    }
+    // Prefetch (independent of x_k) the first kTrsvPrefetch of their L tiles into registers.
+    double pre[kTrsvPrefetch][4];
+#pragma unroll
+    for (int t = 0; t < kTrsvPrefetch; ++t) {
+      if (t < count) {
+        const int ro = (r_first + t * (int)csize) * T, rb = min(T, nrow - ro);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + 256 * q, i = trans ? e % T : e / T, c = trans ? e / T : e % T;
+          pre[t][q] = trsv_tile_el(L, ld, trans, ro, rb, o, tb, i, c);
+        }
+      }
+    }
+    if (owner) {
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, c = e % T;
-        Lk[i][c] = (i < tb && c <= i) ? L[(int64_t)(o + i) * ld + o + c] : 0.0;
+        Ld[i][c] = (i < tb && c <= i) ? L[(int64_t)(o + i) * ld + o + c] : 0.0;
       }
       __syncthreads();
-      if (tid < tb) rdiag[tid] = 1.0 / Lk[tid][tid];
+      if (tid < tb) rdiag[tid] = 1.0 / Ld[tid][tid];
       __syncthreads();
       for (int q = warp; q < R; q += 8) {
         double xi = lane < tb ? x[(int64_t)(o + lane) * ldx + q] : 0.0;
@@ -634,13 +979,13 @@ __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int6
           for (int j = 0; j < tb; ++j) {
             const double xj = __shfl_sync(0xffffffffu, xi, j) * rdiag[j];
             if (lane == j) xi = xj;
-            else if (lane > j) xi -= Lk[lane][j] * xj;
+            else if (lane > j) xi -= Ld[lane][j] * xj;
           }
         } else {
           for (int j = tb - 1; j >= 0; --j) {
             const double xj = __shfl_sync(0xffffffffu, xi, j) * rdiag[j];
             if (lane == j) xi = xj;
-            else if (lane < j) xi -= Lk[j][lane] * xj;
+            else if (lane < j) xi -= Ld[j][lane] * xj;
           }
         }
         if (lane < tb) x[(int64_t)(o + lane) * ldx + q] = xi;
@@ -648,28 +993,41 @@ __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int6
     }
     cluster_sync_all();
     for (int e = tid; e < tb * R; e += blockDim.x) Xk[e / R][e % R] = x[(int64_t)(o + e / R) * ldx + e % R];
-    __syncthreads();
-    for (int r = (int)rank; r < nt; r += (int)csize) {
-      if ((!trans && r <= k) || (trans && r >= k)) continue;
-      const int ro = r * T, rb = min(T, nrow - ro);
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        if (!trans) {
-          const int i = e / T, c = e % T;
-          Lk[i][c] = (i < rb && c < tb) ? L[(int64_t)(ro + i) * ld + o + c] : 0.0;
+#pragma unroll
+    for (int t = 0; t < kTrsvPrefetch + 1; ++t) {
+      // t < kTrsvPrefetch: one prefetched tile; t == kTrsvPrefetch: every remaining tile, loaded here
+      const int tend = t < kTrsvPrefetch ? min(count, t + 1) : count;
+      for (int u = t; u < tend; ++u) {
+        const int ro = (r_first + u * (int)csize) * T, rb = min(T, nrow - ro);
+        __syncthreads();  // Xk written; previous tile's Lk reads done
+        if (t < kTrsvPrefetch) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, i = trans ? e % T : e / T, c = trans ? e / T : e % T;
+            Lk[i][c] = pre[t][q];
+          }
         } else {
-          const int c = e / T, i = e % T;  // L[o+c][ro+i] = (L^T)[ro+i][o+c]
-          Lk[i][c] = (i < rb && c < tb) ? L[(int64_t)(o + c) * ld + ro + i] : 0.0;
+          for (int e = tid; e < T * T; e += blockDim.x) {
+            const int i = trans ? e % T : e / T, c = trans ? e / T : e % T;
+            Lk[i][c] = trsv_tile_el(L, ld, trans, ro, rb, o, tb, i, c);
+          }
+        }
+        __syncthreads();
+        for (int e = tid; e < rb * R; e += blockDim.x) {
+          const int i = e / R, q = e % R;
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // four chains over c
+          for (int c = 0; c < tb; c += 4) {
+            a0 = fma(Lk[i][c], Xk[c][q], a0);
+            if (c + 1 < tb) a1 = fma(Lk[i][c + 1], Xk[c + 1][q], a1);
+            if (c + 2 < tb) a2 = fma(Lk[i][c + 2], Xk[c + 2][q], a2);
+            if (c + 3 < tb) a3 = fma(Lk[i][c + 3], Xk[c + 3][q], a3);
+          }
+          x[(int64_t)(ro + i) * ldx + q] -= (a0 + a1) + (a2 + a3);
         }
       }
-      __syncthreads();
-      for (int e = tid; e < rb * R; e += blockDim.x) {
-        const int i = e / R, q = e % R;
-        double acc = 0.0;
-        for (int c = 0; c < tb; ++c) acc += Lk[i][c] * Xk[c][q];
-        x[(int64_t)(ro + i) * ldx + q] -= acc;
-      }
-      __syncthreads();
+      if (t < kTrsvPrefetch) continue;
     }
+    __syncthreads();
   }
 }
 

@@ -389,126 +389,161 @@ __device__ __forceinline__ const double* part_base(const SplitArgs& a, int zl) {
   return a.X + (int64_t)(z % a.nb1) * a.s1 + (int64_t)(z / a.nb1) * a.s2;
 }
 
-// Row maxima of |x| (FP64 bit patterns are order-preserving for non-negative
-// values): each CTA reduces 32 rows over a 256-wide k slab and merges with atomicMax.
-__global__ void __launch_bounds__(256) split_rowmax_kernel(SplitArgs a) {
-  const int zl = blockIdx.z;
+// One operand side (op(A) rows m, or op(B)^T rows n): up to two parts along k.
+struct SplitOp {
+  SplitArgs part[kMaxTerms];
+  int nparts;
+};
+
+__device__ __forceinline__ double load_el(const SplitArgs& a, const double* X, int r, int k) {
+  return (r < a.R && k < a.Kc && !masked(a, r, k)) ? X[(int64_t)r * a.sr + (int64_t)k * a.sk] : 0.0;
+}
+
+// Digits of one value (OZ) with the row's max bit pattern mb; returns the s slice values.
+__device__ __forceinline__ void oz_digits(double x, unsigned long long mb, int s, float* dig) {
+  const int emax = (int)(mb >> 52);  // biased exponent of the row max
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  long long Y = 0;
+  if (emax > 0 && emax < 2047 && ex > 0) {
+    // |x| = M 2^(ex-1075); row scale 2^e with e = emax - 1021 puts |x| 2^-e below 1/2;
+    // Y = round(|x| 2^(7s - e)) = round(M 2^sh), sh <= 7s - 54 < 0.
+    const long long M = (bits & 0x000fffffffffffffll) | 0x0010000000000000ll;
+    const int e = emax - 1021;
+    const int sh = ex - 1075 + 7 * s - e;
+    if (sh >= 0) Y = M << sh;
+    else if (sh > -64) Y = (M + (1ll << (-sh - 1))) >> (-sh);
+    if (bits < 0) Y = -Y;
+  }
+  // Balanced base-128 digits, least significant first: d_s ... d_2 in [-64, 63], d_1 the rest.
+  for (int p = s - 1; p >= 1; --p) {
+    const long long d = ((Y + 64) & 127) - 64;
+    dig[p] = (float)d;
+    Y = (Y - d) >> 7;
+  }
+  dig[0] = (float)Y;
+}
+
+// Part of `op` holding concatenated column k (parts start on 32-column boundaries).
+__device__ __forceinline__ int part_of(const SplitOp& op, int k) {
+  int pi = 0;
+  while (pi + 1 < op.nparts && k >= op.part[pi + 1].kout0) ++pi;
+  return pi;
+}
+
+// Row maxima of |x| over the concatenated k range, both operands in one launch:
+// blockIdx.z = 2 * batch entry + side; each CTA reduces 32 rows over a 256-wide
+// slab and merges with atomicMax (FP64 bit patterns order |x|).
+__global__ void __launch_bounds__(256) split_rowmax_kernel(SplitOp sa_op, SplitOp sb_op,
+                                                           unsigned long long* rmA,
+                                                           unsigned long long* rmB) {
+  const int side = blockIdx.z & 1, zl = blockIdx.z >> 1;
+  const SplitOp& op = side == 0 ? sa_op : sb_op;
+  unsigned long long* rm = side == 0 ? rmA : rmB;
+  const SplitArgs& a0 = op.part[0];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 256;
-  const double* Xz = part_base(a, zl);
+  if (r0 >= a0.Rpad || k0 >= a0.Kp) return;
   __shared__ unsigned long long red[8][32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int kend = min(a.Kc, k0 + 256);
-  if (a.sk == 1) {
-    // k contiguous: warp w takes rows r0 + w + 8j, lanes stride k
-    for (int rr = w; rr < 32; rr += 8) {
-      const int r = r0 + rr;
-      unsigned long long mr = 0;
-      if (r < a.R)
-        for (int k = k0 + lane; k < kend; k += 32) {
-          if (masked(a, r, k)) continue;
+  unsigned long long m = 0;
+  for (int pi = 0; pi < op.nparts; ++pi) {
+    const SplitArgs& a = op.part[pi];
+    const int lo = max(k0, a.kout0), hi = min(k0 + 256, a.kout0 + a.Kc);
+    if (lo >= hi) continue;
+    const double* X = part_base(a, zl);
+    if (a.sk == 1) {
+      for (int rr = w; rr < 32; rr += 8) {
+        const int r = r0 + rr;
+        unsigned long long mr = 0;
+        for (int kc = lo + lane; kc < hi; kc += 32) {
           const unsigned long long v =
-              (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + k]) & 0x7fffffffffffffffull;
+              (unsigned long long)__double_as_longlong(load_el(a, X, r, kc - a.kout0)) & 0x7fffffffffffffffull;
           mr = v > mr ? v : mr;
         }
-      for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mr, off);
-        mr = o > mr ? o : mr;
+        for (int off = 16; off > 0; off >>= 1) {
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, mr, off);
+          mr = o > mr ? o : mr;
+        }
+        if (lane == 0 && mr) atomicMax(&rm[(int64_t)zl * a0.Rpad + r], mr);
       }
-      if (lane == 0 && r < a.R && mr) atomicMax(&a.rowmax[(int64_t)zl * a.Rpad + r], mr);
-    }
-  } else {
-    // rows contiguous: lane = row, warps split the slab
-    const int r = r0 + lane;
-    unsigned long long m = 0;
-    if (r < a.R)
-      for (int k = k0 + w; k < kend; k += 8) {
-        if (masked(a, r, k)) continue;
+    } else {
+      const int r = r0 + lane;
+      for (int kc = lo + w; kc < hi; kc += 8) {
         const unsigned long long v =
-            (unsigned long long)__double_as_longlong(Xz[(int64_t)r * a.sr + (int64_t)k * a.sk]) &
-            0x7fffffffffffffffull;
+            (unsigned long long)__double_as_longlong(load_el(a, X, r, kc - a.kout0)) & 0x7fffffffffffffffull;
         m = v > m ? v : m;
       }
-    red[w][lane] = m;
-    __syncthreads();
-    if (w == 0) {
-      for (int ww = 1; ww < 8; ++ww) m = red[ww][lane] > m ? red[ww][lane] : m;
-      if (r < a.R && m) atomicMax(&a.rowmax[(int64_t)zl * a.Rpad + r], m);
     }
+  }
+  red[w][lane] = m;
+  __syncthreads();
+  if (w == 0) {
+    for (int ww = 1; ww < 8; ++ww) m = red[ww][lane] > m ? red[ww][lane] : m;
+    if (m) atomicMax(&rm[(int64_t)zl * a0.Rpad + r0 + lane], m);
   }
 }
 
-// Digit slices (OZ) or hi/lo slices (X3) of a 32 x 32 tile of one part. The
-// first part also writes the row scales (after every part's row maxima).
-__global__ void __launch_bounds__(256) split_digits_kernel(SplitArgs a, int write_scale) {
-  __shared__ double tile[32][33];
-  const int zl = blockIdx.z;
+// Slices of one 32 x 32 tile of the concatenated operand (blockIdx.z = 2 * batch
+// entry + side), plus the row scales (first column of tiles) and, for side A, the
+// zeroing of the int64 accumulator rows.
+__global__ void __launch_bounds__(256) split_digits_kernel(SplitOp sa_op, SplitOp sb_op,
+                                                           const unsigned long long* rmA,
+                                                           const unsigned long long* rmB,
+                                                           long long* T, int Tcols) {
+  const int side = blockIdx.z & 1, zl = blockIdx.z >> 1;
+  const SplitOp& op = side == 0 ? sa_op : sb_op;
+  const unsigned long long* rm = side == 0 ? rmA : rmB;
+  const SplitArgs& a0 = op.part[0];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const double* Xz = part_base(a, zl);
+  if (r0 >= a0.Rpad || c0 >= a0.Kp) return;
+  __shared__ double tile[32][33];
+  __shared__ unsigned long long rmax[32];
   const int tid = threadIdx.x;
-  for (int e = tid; e < 32 * 32; e += 256) {
+  const int pi = part_of(op, c0);
+  const SplitArgs& a = op.part[pi];
+  const double* X = part_base(a, zl);
+  const int kc0 = c0 - a.kout0;  // column within the part
+  if (tid < 32) rmax[tid] = a0.mode == TC_OZ ? rm[(int64_t)zl * a0.Rpad + r0 + tid] : 0ull;
+  for (int e = tid; e < 1024; e += 256) {
     int i, j;
     if (a.sk == 1) { i = e / 32; j = e % 32; } else { j = e / 32; i = e % 32; }
-    const int r = r0 + i, k = c0 + j;
-    tile[i][j] = (r < a.R && k < a.Kc && !masked(a, r, k)) ? Xz[(int64_t)r * a.sr + (int64_t)k * a.sk] : 0.0;
+    tile[i][j] = load_el(a, X, r0 + i, kc0 + j);
   }
   __syncthreads();
-  const int kw = ((a.Kc + 31) / 32) * 32;  // this part's padded width
-  for (int e = tid; e < 32 * 32; e += 256) {
+  const int64_t plane = (int64_t)a0.Rpad * a0.Kp;
+  for (int e = tid; e < 1024; e += 256) {
     const int i = e / 32, j = e % 32;
-    const int r = r0 + i, k = c0 + j;
-    if (r >= a.Rpad || k >= kw) continue;
+    __nv_bfloat16* o = a0.out + (((int64_t)zl * a0.s) * a0.Rpad + r0 + i) * a0.Kp + c0 + j;
     const double x = tile[i][j];
-    __nv_bfloat16* o = a.out + (((int64_t)zl * a.s) * a.Rpad + r) * a.Kp + a.kout0 + k;
-    const int64_t plane = (int64_t)a.Rpad * a.Kp;
-    if (a.mode == TC_X3) {
+    if (a0.mode == TC_X3) {
       const float xf = (float)x;
       const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
       o[0] = hi;
-      o[plane] = lo;
+      o[plane] = __float2bfloat16_rn(xf - __bfloat162float(hi));
       continue;
     }
-    // Ozaki digits by integer arithmetic on the FP64 fields.
-    const unsigned long long mb = r < a.R ? a.rowmax[(int64_t)zl * a.Rpad + r] : 0ull;
-    const int emax = (int)(mb >> 52);           // biased exponent of the row max
-    const long long bits = __double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    long long Y = 0;
-    if (emax > 0 && emax < 2047 && ex > 0) {
-      // |x| = M 2^(ex-1075); row scale 2^e with e = emax - 1021 puts |x| 2^-e below 1/2;
-      // Y = round(|x| 2^(7s - e)) = round(M 2^sh), sh <= 7s - 54 < 0.
-      const long long M = (bits & 0x000fffffffffffffll) | 0x0010000000000000ll;
-      const int e = emax - 1021;
-      const int sh = ex - 1075 + 7 * a.s - e;
-      if (sh >= 0) Y = M << sh;
-      else if (sh > -64) Y = (M + (1ll << (-sh - 1))) >> (-sh);
-      if (bits < 0) Y = -Y;
-    }
-    // Balanced base-128 digits, least significant first: d_s ... d_2 in [-64, 63], d_1 the rest.
     float dig[8];
-    for (int p = a.s - 1; p >= 1; --p) {
-      long long d = ((Y + 64) & 127) - 64;
-      dig[p] = (float)d;
-      Y = (Y - d) >> 7;
-    }
-    dig[0] = (float)Y;
+    oz_digits(x, rmax[i], a0.s, dig);
     float sc = 1.0f / 128.0f;
-    for (int p = 0; p < a.s; ++p) {
+    for (int p = 0; p < a0.s; ++p) {
       o[p * plane] = __float2bfloat16_rn(dig[p] * sc);  // exact: |d| <= 65, power-of-two scale
       sc *= 1.0f / 128.0f;
     }
   }
-  if (write_scale && blockIdx.x == 0 && tid < 32) {
-    const int r = r0 + tid;
-    if (r < a.Rpad) {
+  if (blockIdx.x == 0) {
+    if (tid < 32) {
+      const int r = r0 + tid;
       double sc = 1.0;
-      if (a.mode == TC_OZ && r < a.R) {
-        const unsigned long long mb = a.rowmax[(int64_t)zl * a.Rpad + r];
-        const int emax = (int)(mb >> 52);
+      if (a0.mode == TC_OZ && r < a0.R) {
+        const int emax = (int)(rmax[tid] >> 52);
         if (emax == 2047) sc = __longlong_as_double(0x7ff8000000000000ll);  // NaN/Inf row
         else if (emax > 0) sc = ldexp(1.0, emax - 1021);
       }
-      a.scale[(int64_t)zl * a.Rpad + r] = sc;
+      a0.scale[(int64_t)zl * a0.Rpad + r] = sc;
+    }
+    if (side == 0 && T) {
+      long long* Tz = T + ((int64_t)zl * a0.Rpad + r0) * Tcols;
+      for (int64_t e = tid; e < (int64_t)32 * Tcols; e += 256) Tz[e] = 0;
     }
   }
 }
@@ -604,54 +639,46 @@ struct Part {
   int mask;  // see SplitArgs::mask
 };
 
-static cudaError_t split_parts(const Part* parts, int np, int nb1, int zbase, int R, int Kp, int Rpad,
-                               int s, int mode, int nb, __nv_bfloat16* out, double* scale,
-                               unsigned long long* rowmax, cudaStream_t st) {
-  TimedLaunch tl(K_TC_SPLIT, 0.0, st);
-  SplitArgs a[2];
+static void fill_op(SplitOp* op, const Part* parts, int np, int nb1, int zbase, int R, int Kp,
+                    int Rpad, int s, int mode, int nb, __nv_bfloat16* out, double* scale) {
+  op->nparts = np;
   int k0 = 0;
   for (int i = 0; i < np; ++i) {
-    a[i] = SplitArgs{};
-    a[i].X = parts[i].X; a[i].sr = parts[i].sr; a[i].sk = parts[i].sk;
-    a[i].s1 = parts[i].s1; a[i].s2 = parts[i].s2; a[i].nb1 = nb1; a[i].zbase = zbase;
-    a[i].R = R; a[i].Kc = parts[i].K; a[i].kout0 = k0; a[i].Kp = Kp;
-    a[i].Rpad = Rpad; a[i].s = s; a[i].mode = mode; a[i].nb = nb;
-    a[i].out = out; a[i].scale = scale; a[i].rowmax = rowmax; a[i].mask = parts[i].mask;
+    SplitArgs& a = op->part[i];
+    a = SplitArgs{};
+    a.X = parts[i].X; a.sr = parts[i].sr; a.sk = parts[i].sk;
+    a.s1 = parts[i].s1; a.s2 = parts[i].s2; a.nb1 = nb1; a.zbase = zbase;
+    a.R = R; a.Kc = parts[i].K; a.kout0 = k0; a.Kp = Kp;
+    a.Rpad = Rpad; a.s = s; a.mode = mode; a.nb = nb;
+    a.out = out; a.scale = scale; a.rowmax = nullptr; a.mask = parts[i].mask;
     k0 += (int)rup(parts[i].K, BK);
   }
-  if (mode == TC_OZ) {
-    cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)nb * Rpad * 8, st);
-    if (e != cudaSuccess) return e;
-    for (int i = 0; i < np; ++i)
-      split_rowmax_kernel<<<dim3((parts[i].K + 255) / 256, (Rpad + 31) / 32, nb), 256, 0, st>>>(a[i]);
-  }
-  for (int i = 0; i < np; ++i)
-    split_digits_kernel<<<dim3((unsigned)((rup(parts[i].K, BK) + 31) / 32), (Rpad + 31) / 32, nb), 256, 0,
-                          st>>>(a[i], i == 0);
-  return cudaGetLastError();
 }
 
 static int g_smem_attr_set = 0;
 
 cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (g.nterms < 1 || g.nterms > 2) return cudaErrorInvalidValue;
-  // Two terms are one product over the concatenated k range when they share alpha
-  // and neither operand is triangular; otherwise they run one after the other.
-  const bool concat = g.nterms == 2 && g.t[0].alpha == g.t[1].alpha && g.t[0].triA == TRI_NONE &&
-                      g.t[0].triB == TRI_NONE && g.t[1].triA == TRI_NONE && g.t[1].triB == TRI_NONE;
-  if (g.nterms == 2 && !concat) {
-    GemmArgs g0 = g, g1 = g;
-    g0.nterms = 1;
-    g1.t[0] = g.t[1];
-    g1.nterms = 1;
-    g1.beta = 1.0;
-    cudaError_t e = gemm_tc(g0, mode, ws, ws_bytes, s);
-    return e != cudaSuccess ? e : gemm_tc(g1, mode, ws, ws_bytes, s);
+  if (g.nterms < 1 || g.nterms > kMaxTerms) return cudaErrorInvalidValue;
+  // Several terms are one product over the concatenated k range when they share
+  // alpha and no operand is triangular; otherwise they run one after the other.
+  bool concat = g.nterms > 1;
+  for (int i = 0; i < g.nterms && concat; ++i)
+    concat = g.t[i].alpha == g.t[0].alpha && g.t[i].triA == TRI_NONE && g.t[i].triB == TRI_NONE;
+  if (g.nterms > 1 && !concat) {
+    for (int i = 0; i < g.nterms; ++i) {
+      GemmArgs gi = g;
+      gi.t[0] = g.t[i];
+      gi.nterms = 1;
+      if (i > 0) gi.beta = 1.0;
+      cudaError_t e = gemm_tc(gi, mode, ws, ws_bytes, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   const int S = tc_slices(mode);
   const int M = g.M, N = g.N;
   if (M <= 0 || N <= 0) return cudaSuccess;
-  Part pa[2], pb[2];
+  Part pa[kMaxTerms], pb[kMaxTerms];
   int Kp = 0;
   for (int i = 0; i < g.nterms; ++i) {
     const GemmTerm& t = g.t[i];
@@ -715,12 +742,21 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     unsigned long long* rmB = rmA + (int64_t)nb * Mp;
     w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
     long long* Tacc = (long long*)w;
-    cudaError_t e = split_parts(pa, g.nterms, g.nb1, c0, M, Kp, Mp, S, mode, nb, As, sa, rmA, s);
-    if (e != cudaSuccess) return e;
-    e = split_parts(pb, g.nterms, g.nb1, c0, N, Kp, Np, S, mode, nb, Bs, sb, rmB, s);
-    if (e != cudaSuccess) return e;
-    if (mode == TC_OZ) {
-      e = cudaMemsetAsync(Tacc, 0, (size_t)nb * Mp * Np * 8, s);
+    SplitOp opA, opB;
+    fill_op(&opA, pa, g.nterms, g.nb1, c0, M, Kp, Mp, S, mode, nb, As, sa);
+    fill_op(&opB, pb, g.nterms, g.nb1, c0, N, Kp, Np, S, mode, nb, Bs, sb);
+    cudaError_t e;
+    {
+      TimedLaunch tl(K_TC_SPLIT, 0.0, s);
+      const int bands = (Mp > Np ? Mp : Np) / 32;
+      if (mode == TC_OZ) {
+        e = cudaMemsetAsync(rmA, 0, ((size_t)Mp + Np) * nb * 8, s);
+        if (e != cudaSuccess) return e;
+        split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, 2 * nb), 256, 0, s>>>(opA, opB, rmA, rmB);
+      }
+      split_digits_kernel<<<dim3(Kp / 32, bands, 2 * nb), 256, 0, s>>>(
+          opA, opB, rmA, rmB, mode == TC_OZ ? Tacc : nullptr, Np);
+      e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     CUtensorMap mA, mB;

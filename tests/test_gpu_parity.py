@@ -19,6 +19,7 @@ SHAPES = [
     (16, 32, 4),    # the n=16, b=32, a=4 workload
     (1, 5, 3), (1, 40, 0), (2, 33, 1), (3, 45, 7), (4, 64, 0), (5, 70, 13),
     (7, 100, 33), (3, 96, 40), (9, 17, 2), (6, 128, 8), (2, 1, 1), (4, 1, 0),
+    (3, 200, 5), (2, 300, 0), (4, 160, 17),  # single-launch cooperative POTRF, ragged last tile
 ]
 
 
@@ -88,12 +89,14 @@ def test_non_default_stream_and_repeat_bits():
         assert np.array_equal(x, y)  # deterministic: identical bits on a repeat
 
 
+@pytest.mark.parametrize("b", [40, 160])
 @pytest.mark.parametrize("where", ["block0", "block2", "tip"])
-def test_non_spd_reports_lapack_info(where):
-    n, b, a = 4, 40, 3
+def test_non_spd_reports_lapack_info(where, b):
+    n, a = 4, 3
     d, l, ar, t = gen.make_bta(n, b, a, seed=9)
     if where == "block0":
         d[0][5, 5] = -50.0
+        d[0][b - 3, b - 3] = -50.0  # a later failure in the same block must not win
     elif where == "block2":
         d[2] = -d[2]
     else:
