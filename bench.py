@@ -59,7 +59,7 @@ def flops_solve(n, b, a, r):
 
 
 KERNELS = ["gemm_f64", "potrf_panel", "trsm_panel", "tile_inv", "zero_upper", "mirror", "logdet", "trsv",
-           "gemv", "arrow", "probe", "gemm_tc", "tc_split", "tc_final"]
+           "gemv", "arrow", "probe", "gemm_tc", "tc_split", "tc_final", "factor_step"]
 # tensor-core products per FP64 product in each precision mode
 TC_PAIRS = {"ozaki": 28, "bf16x3": 3}
 PREC_DTYPE = {"fp64": "f64", "ozaki": "bf16 slices x7 (FP64-emulated, Ozaki splitting)",

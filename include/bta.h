@@ -299,6 +299,7 @@ int bta_tc_status(int* timed_out);
                                   lower-only outputs) */
 #define BTA_KERNEL_TC_SPLIT 12 /* FP64 -> BF16 slice splitting */
 #define BTA_KERNEL_TC_FINAL 13 /* int64 accumulator -> FP64 output */
+#define BTA_KERNEL_FACTOR_STEP 14 /* one fused block step of the FP64 factorization */
 
 /*
  * bta_timing_enable -- on != 0: from now on every kernel launch of the library

@@ -181,6 +181,19 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   TcWs tw;
   tw.p = w.tc;
   tw.bytes = w.tc_bytes;
+  if (coop && b >= kCoopMinB && prec == BTA_PREC_FP64) {
+    // One fused launch per block step: tile Cholesky of the block column with
+    // the Schur updates of the next block, its arrow block and the tip.
+    for (int64_t i = 0; i < n; ++i) {
+      const bool nx = i + 1 < n;
+      BTA_TRY(factor_step_coop(diag + i * bb, nx ? lower + i * bb : nullptr,
+                               nx ? diag + (i + 1) * bb : nullptr, a > 0 ? arrow + i * a * b : nullptr,
+                               (a > 0 && nx) ? arrow + (i + 1) * a * b : nullptr, a > 0 ? tip : nullptr,
+                               B, Aa, nx ? 1 : 0, i * b, w.coop, s));
+    }
+    if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
+    return 0;
+  }
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
     if (coop && b >= kCoopMinB)

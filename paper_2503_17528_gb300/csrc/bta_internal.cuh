@@ -62,6 +62,13 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
 constexpr size_t kCoopScratch = 256 + 2 * T * T * sizeof(double);
 cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
                        cudaStream_t s);
+// One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}
+// and L_{n,i} in place, and the Schur updates of A_{i+1,i+1}, A_{n,i+1} and the
+// tip (lower tiles). next == 0 for the last block (Lw, D1, Ar1 unused); a == 0:
+// no arrowhead. scratch: kCoopScratch bytes, 256-byte aligned.
+cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
+                             double* tip, int b, int a, int next, long long info_row0,
+                             void* scratch, cudaStream_t s);
 // Reads and clears the timeout flag of the cooperative kernels' grid barriers.
 cudaError_t wait_error_read_reset(int* out);
 

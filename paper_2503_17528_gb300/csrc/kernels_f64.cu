@@ -536,6 +536,7 @@ __device__ __forceinline__ void coop_tile_update(double* C, int64_t ld, int rows
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gq = lane >> 2, tq = lane & 3;
   const int m0 = (warp >> 1) * 8, n0 = (warp & 1) * 16;
+  if (m0 >= rows || n0 >= cols) return;  // warp-uniform: nothing of this warp's part is stored
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   for (int ks = 0; ks < kb; ks += 4) {
     const double a = P[m0 + gq][ks + tq];
@@ -709,6 +710,241 @@ cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, voi
   void* args[] = {&p};
   TimedLaunch tl(K_POTRF_TILE, 0.0, s);
   return cudaLaunchCooperativeKernel((void*)potrf_coop_kernel, dim3(G), dim3(256), args, 0, s);
+}
+
+// ---------------------------------------------------------------------------
+// One block step i of the factorization (Algorithm 1) in one cooperative
+// launch. The block column [A_ii; A_{i+1,i}; A_{n,i}] is factored as a
+// right-looking tile Cholesky whose trailing updates also reach the blocks
+// that step i's Schur complement modifies:
+//   A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T,  A_{n,i+1} -= L_{n,i} L_{i+1,i}^T,
+//   A_nn -= L_{n,i} L_{n,i}^T.
+// Tiles are indexed over the "extended" rows: the tiles of block i, then those
+// of block i+1, then the arrow rows. At tile step k (a column of block i):
+//   A. 16-row slices of every tile (r, k), r > k, solve X L_kk^T = A(r, k)
+//      (this covers the POTRF panel, the TRSM of L_{i+1,i} and of L_{n,i});
+//   B. every lower tile (r, c), r >= c > k, takes -= L(r,k) L(c,k)^T; CTA 0
+//      takes tile (k+1, k+1) first and factors it (look-ahead).
+// The TRSM needs no inverse of L_ii, and the Schur products run as part of the
+// same tile sweep, so the latency-bound tile steps of the POTRF overlap with
+// the bulk of the step's work.
+// ---------------------------------------------------------------------------
+struct StepArgs {
+  double* D0;   // A_ii (b x b): L_ii on return, strict upper triangle zeroed
+  double* Lw;   // A_{i+1,i} (b x b): L_{i+1,i}; unused when next == 0
+  double* D1;   // A_{i+1,i+1} (b x b): lower tiles updated
+  double* Ar0;  // A_{n,i} (a x b): L_{n,i}
+  double* Ar1;  // A_{n,i+1} (a x b): updated; unused when next == 0
+  double* tip;  // A_nn (a x a): lower tiles updated
+  int b, a, nt, na, next;
+  long long row0;  // 1-based global row of block i's first row, minus one
+  CoopBar* bar;
+  double* rdiag;  // [2][T]: 1 / L_jj of the current diagonal tile (by step parity)
+};
+
+// Group of an extended tile row (0: block i, 1: block i+1, 2: arrow) and its
+// tile index inside the group.
+__device__ __forceinline__ int ext_group(const StepArgs& p, int r, int& lr) {
+  if (r < p.nt) {
+    lr = r;
+    return 0;
+  }
+  r -= p.nt;
+  if (p.next) {
+    if (r < p.nt) {
+      lr = r;
+      return 1;
+    }
+    r -= p.nt;
+  }
+  lr = r;
+  return 2;
+}
+
+__device__ __forceinline__ int ext_rows(const StepArgs& p, int r) {
+  int lr;
+  const int g = ext_group(p, r, lr);
+  return min(T, (g == 2 ? p.a : p.b) - T * lr);
+}
+
+// Address and leading dimension of tile (r, c), r >= c, of the extended lower triangle.
+__device__ __forceinline__ double* ext_tile(const StepArgs& p, int r, int c, int64_t& ld) {
+  int lr, lc;
+  const int gr = ext_group(p, r, lr), gc = ext_group(p, c, lc);
+  if (gc == 2) {
+    ld = p.a;
+    return p.tip + (int64_t)(T * lr) * p.a + T * lc;
+  }
+  ld = p.b;
+  double* base;
+  if (gc == 0)
+    base = gr == 0 ? p.D0 : (gr == 1 ? p.Lw : p.Ar0);
+  else
+    base = gr == 1 ? p.D1 : p.Ar1;
+  return base + (int64_t)(T * lr) * p.b + T * lc;
+}
+
+__global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
+  __shared__ double S[T][T + 1];
+  __shared__ double P[T][T + 1];
+  __shared__ double Q[T][T + 1];
+  __shared__ double rd[T];
+  const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
+  const int nt = p.nt, E = nt * (1 + p.next) + p.na;
+  const int64_t b = p.b;
+  unsigned gen = 0;
+
+  if (bid == 0) {  // step 0's diagonal tile
+    const int tb = min(T, p.b);
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      S[i][j] = (i < tb && j <= i) ? p.D0[(int64_t)i * b + j] : 0.0;
+    }
+    __syncthreads();
+    coop_factor(S, rd, tb, p.row0);
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      if (i < tb && j < tb) p.D0[(int64_t)i * b + j] = S[i][j];
+    }
+    if (tid < T) p.rdiag[tid] = rd[tid];
+  }
+  grid_barrier(p.bar, G, gen);
+  for (int k = 0; k < nt; ++k) {
+    const int o = k * T, tbk = min(T, p.b - o);
+    const double* rdk = p.rdiag + (k & 1) * T;
+    const double* Lkk = p.D0 + (int64_t)o * b + o;
+    // A. panel slices (16 rows) of the tiles below (k, k).
+    const int nslices = 2 * (E - k - 1);
+    for (int sl = bid; sl < nslices; sl += G) {
+      const int r = k + 1 + sl / 2, rs = (sl % 2) * 16;
+      const int rows = min(16, ext_rows(p, r) - rs);
+      if (rows <= 0) continue;  // uniform over the CTA
+      int64_t ldx;
+      double* X = ext_tile(p, r, k, ldx) + (int64_t)rs * ldx;
+      __syncthreads();
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        Q[i][j] = (i < tbk && j <= i) ? Lkk[(int64_t)i * b + j] : 0.0;
+        if (i < 16) P[i][j] = (i < rows && j < tbk) ? X[(int64_t)i * ldx + j] : 0.0;
+      }
+      if (tid < T) rd[tid] = rdk[tid];
+      __syncthreads();
+      for (int j = 0; j < tbk; ++j) {
+        if (tid < rows) P[tid][j] *= rd[j];
+        __syncthreads();
+        const int w = tbk - j - 1;
+        for (int e = tid; e < rows * w; e += blockDim.x) {
+          const int i = e / w, c = j + 1 + e % w;
+          P[i][c] -= P[i][j] * Q[c][j];
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < rows * tbk; e += blockDim.x) {
+        const int i = e / tbk, c = e % tbk;
+        X[(int64_t)i * ldx + c] = P[i][c];
+      }
+    }
+    grid_barrier(p.bar, G, gen);
+    const int m = E - k - 1;  // extended tiles below k
+    if (m == 0) break;        // last block without arrowhead: nothing trails the last panel
+    // B. trailing updates of step k.
+    const bool look = k + 1 < nt && G > 1;
+    if (look && bid == 0) {
+      const int o1 = o + T, tb1 = min(T, p.b - o1);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        P[i][j] = (i < tb1 && j < tbk) ? p.D0[(int64_t)(o1 + i) * b + o + j] : 0.0;
+        S[i][j] = (i < tb1 && j <= i) ? p.D0[(int64_t)(o1 + i) * b + o1 + j] : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (j <= i && i < tb1) {
+          double acc = 0.0;
+          for (int c = 0; c < tbk; ++c) acc = fma(P[i][c], P[j][c], acc);
+          S[i][j] -= acc;
+        }
+      }
+      __syncthreads();
+      coop_factor(S, rd, tb1, p.row0 + o1);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (i < tb1 && j < tb1) p.D0[(int64_t)(o1 + i) * b + o1 + j] = S[i][j];
+      }
+      if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
+    } else {
+      const long long ntiles = (long long)m * (m + 1) / 2;
+      const int workers = look ? G - 1 : G, wid = look ? bid - 1 : bid;
+      for (long long t = (look ? 1 : 0) + wid; t < ntiles; t += workers) {
+        int rr = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(rr + 1) * (rr + 2) / 2 <= t) ++rr;
+        while ((long long)rr * (rr + 1) / 2 > t) --rr;
+        const int cc = (int)(t - (long long)rr * (rr + 1) / 2);
+        const int r = k + 1 + rr, c = k + 1 + cc;
+        const int rb = ext_rows(p, r), cb = ext_rows(p, c);
+        int64_t ldr, ldq, ldc;
+        const double* Lr = ext_tile(p, r, k, ldr);
+        const double* Lc = ext_tile(p, c, k, ldq);
+        double* C = ext_tile(p, r, c, ldc);
+        __syncthreads();
+        for (int e = tid; e < T * T; e += blockDim.x) {
+          const int i = e / T, j = e % T;
+          P[i][j] = (i < rb && j < tbk) ? Lr[(int64_t)i * ldr + j] : 0.0;
+          Q[i][j] = (i < cb && j < tbk) ? Lc[(int64_t)i * ldq + j] : 0.0;
+        }
+        __syncthreads();
+        coop_tile_update(C, ldc, rb, cb, P, Q, T);
+      }
+    }
+    grid_barrier(p.bar, G, gen);
+  }
+  for (long long e = (long long)bid * blockDim.x + tid; e < (long long)p.b * p.b;
+       e += (long long)G * blockDim.x) {
+    const int i = (int)(e / p.b), j = (int)(e % p.b);
+    if (j > i) p.D0[(int64_t)i * b + j] = 0.0;
+  }
+}
+
+static int step_grid() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_step_kernel, 256, 0);
+    // Two CTAs per SM: one CTA's tile loads overlap the other's DMMA work.
+    cached = per >= 2 ? 2 * sms : (per >= 1 ? sms : 0);
+  }
+  return cached;
+}
+
+// Algorithmic flops of one step: POTRF b^3/3, the (b [+ b] + a)-row panel solve
+// (b^2 per row), and the Schur products on the lower triangles they update.
+static double step_flops(double b, double a, int next) {
+  double f = b * b * b / 3.0 + (next ? b : 0.0) * b * b + a * b * b;
+  if (next) f += b * (b + 1) * b + 2.0 * a * b * b;
+  f += a * (a + 1) * b;
+  return f;
+}
+
+cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
+                             double* tip, int b, int a, int next, long long info_row0,
+                             void* scratch, cudaStream_t s) {
+  StepArgs p;
+  p.D0 = D0; p.Lw = Lw; p.D1 = D1; p.Ar0 = Ar0; p.Ar1 = Ar1; p.tip = tip;
+  p.b = b; p.a = a; p.nt = (b + T - 1) / T; p.na = (a + T - 1) / T; p.next = next ? 1 : 0;
+  p.row0 = info_row0;
+  p.bar = (CoopBar*)scratch;
+  p.rdiag = (double*)((char*)scratch + 256);
+  if (b < 1 || a < 0 || (next && (!Lw || !D1 || (a > 0 && !Ar1))) || (a > 0 && (!Ar0 || !tip)))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(CoopBar), s);
+  if (e != cudaSuccess) return e;
+  const int G = step_grid();
+  if (G < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {&p};
+  TimedLaunch tl(K_FACTOR_STEP, timing_on() ? step_flops(b, a, p.next) : 0.0, s);
+  return cudaLaunchCooperativeKernel((void*)factor_step_kernel, dim3(G), dim3(256), args, 0, s);
 }
 
 cudaError_t wait_error_read_reset(int* out) {

@@ -23,6 +23,7 @@ enum KernelId {
   K_GEMM_TC,
   K_TC_SPLIT,
   K_TC_FINAL,
+  K_FACTOR_STEP,
   K_COUNT
 };
 

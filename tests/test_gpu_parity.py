@@ -19,7 +19,8 @@ SHAPES = [
     (16, 32, 4),    # the n=16, b=32, a=4 workload
     (1, 5, 3), (1, 40, 0), (2, 33, 1), (3, 45, 7), (4, 64, 0), (5, 70, 13),
     (7, 100, 33), (3, 96, 40), (9, 17, 2), (6, 128, 8), (2, 1, 1), (4, 1, 0),
-    (3, 200, 5), (2, 300, 0), (4, 160, 17),  # single-launch cooperative POTRF, ragged last tile
+    (3, 200, 5), (2, 300, 0), (4, 160, 17),  # one fused launch per block step, ragged last tile
+    (1, 128, 0), (1, 150, 9), (2, 130, 40), (3, 256, 70),  # one block; arrow rows over 2-3 tiles
 ]
 
 
