@@ -60,6 +60,10 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
 // Cooperative single-launch POTRF of one nrow x nrow block (nrow >= 64 pays);
 // scratch: coop_scratch_bytes, 256-byte aligned.
 constexpr size_t kCoopScratch = 256 + 2 * T * T * sizeof(double);
+// Largest tile count per block order of the fused factor step (b <= 32768); its
+// per-launch flags sit at byte 1024 of the same scratch.
+constexpr int kStepMaxTiles = 1024;
+static_assert(1024 + kStepMaxTiles * sizeof(int) <= kCoopScratch, "step scratch");
 cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
                        cudaStream_t s);
 // One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}

@@ -740,6 +740,7 @@ struct StepArgs {
   long long row0;  // 1-based global row of block i's first row, minus one
   CoopBar* bar;
   double* rdiag;  // [2][T]: 1 / L_jj of the current diagonal tile (by step parity)
+  int* ctr;       // [nt]: tiles taken so far in step k (zeroed per launch)
 };
 
 // Group of an extended tile row (0: block i, 1: block i+1, 2: arrow) and its
@@ -784,12 +785,51 @@ __device__ __forceinline__ double* ext_tile(const StepArgs& p, int r, int c, int
   return base + (int64_t)(T * lr) * p.b + T * lc;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(pred ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Row of the lower-triangular index u (u = row (row + 1) / 2 + col, col <= row).
+__device__ __forceinline__ int tri_row(int u) {
+  int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= u) ++r;
+  while (r * (r + 1) / 2 > u) --r;
+  return r;
+}
+
+// Panel solve in shared memory: X (rows x tb) <- X L^{-T}, L lower in Lt, rdv = 1 / diag(L).
+__device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*Lt)[T + 1],
+                                            const double* rdv, int rows, int tb) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < tb; ++j) {
+    if (tid < rows) X[tid][j] *= rdv[j];
+    __syncthreads();
+    const int w = tb - j - 1;
+    for (int e = tid; e < rows * w; e += blockDim.x) {
+      const int i = e / w, c = j + 1 + e % w;
+      X[i][c] -= X[i][j] * Lt[c][j];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
-  __shared__ double S[T][T + 1];
-  __shared__ double P[T][T + 1];
-  __shared__ double Q[T][T + 1];
+  __shared__ double S[T][T + 1];  // CTA 0: the look-ahead tile
+  __shared__ double Lt[T][T + 1]; // L_kk for the panel slices
+  __shared__ double Pb[2][T][T + 1];
+  __shared__ double Qb[2][T][T + 1];
   __shared__ double rd[T];
+  __shared__ int s_next[2];
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
+  const int wm = (warp >> 1) * 8, wn = (warp & 1) * 16;  // this warp's 8 x 16 part of a tile
   const int nt = p.nt, E = nt * (1 + p.next) + p.na;
   const int64_t b = p.b;
   unsigned gen = 0;
@@ -813,47 +853,44 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
     const int o = k * T, tbk = min(T, p.b - o);
     const double* rdk = p.rdiag + (k & 1) * T;
     const double* Lkk = p.D0 + (int64_t)o * b + o;
-    // A. panel slices (16 rows) of the tiles below (k, k).
-    const int nslices = 2 * (E - k - 1);
+    // A. panel: row slices of the tiles below (k, k), X L_kk^T = A(r, k); the
+    // slices are as short as one round over the grid allows (8, 16 or 32 rows).
+    const int below = E - k - 1;
+    const int per = 4 * below <= G ? 4 : (2 * below <= G ? 2 : 1), sh = T / per;
+    const int nslices = per * below;
+    bool loaded = false;
     for (int sl = bid; sl < nslices; sl += G) {
-      const int r = k + 1 + sl / 2, rs = (sl % 2) * 16;
-      const int rows = min(16, ext_rows(p, r) - rs);
+      const int r = k + 1 + sl / per, rs = (sl % per) * sh;
+      const int rows = min(sh, ext_rows(p, r) - rs);
       if (rows <= 0) continue;  // uniform over the CTA
       int64_t ldx;
-      double* X = ext_tile(p, r, k, ldx) + (int64_t)rs * ldx;
+      double* X = ext_tile(p, r, k, ldx);
+      X += (int64_t)rs * ldx;
       __syncthreads();
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, j = e % T;
-        Q[i][j] = (i < tbk && j <= i) ? Lkk[(int64_t)i * b + j] : 0.0;
-        if (i < 16) P[i][j] = (i < rows && j < tbk) ? X[(int64_t)i * ldx + j] : 0.0;
+        if (!loaded) Lt[i][j] = (i < tbk && j <= i) ? Lkk[(int64_t)i * b + j] : 0.0;
+        S[i][j] = (i < rows && j < tbk) ? X[(int64_t)i * ldx + j] : 0.0;
       }
-      if (tid < T) rd[tid] = rdk[tid];
+      if (!loaded && tid < T) rd[tid] = rdk[tid];
+      loaded = true;
       __syncthreads();
-      for (int j = 0; j < tbk; ++j) {
-        if (tid < rows) P[tid][j] *= rd[j];
-        __syncthreads();
-        const int w = tbk - j - 1;
-        for (int e = tid; e < rows * w; e += blockDim.x) {
-          const int i = e / w, c = j + 1 + e % w;
-          P[i][c] -= P[i][j] * Q[c][j];
-        }
-        __syncthreads();
-      }
+      panel_solve(S, Lt, rd, rows, tbk);
       for (int e = tid; e < rows * tbk; e += blockDim.x) {
         const int i = e / tbk, c = e % tbk;
-        X[(int64_t)i * ldx + c] = P[i][c];
+        X[(int64_t)i * ldx + c] = S[i][c];
       }
     }
     grid_barrier(p.bar, G, gen);
     const int m = E - k - 1;  // extended tiles below k
     if (m == 0) break;        // last block without arrowhead: nothing trails the last panel
-    // B. trailing updates of step k.
-    const bool look = k + 1 < nt && G > 1;
+    // B. trailing updates of step k; CTA 0 takes tile (k+1, k+1) and factors it.
+    const bool look = k + 1 < nt;
     if (look && bid == 0) {
       const int o1 = o + T, tb1 = min(T, p.b - o1);
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, j = e % T;
-        P[i][j] = (i < tb1 && j < tbk) ? p.D0[(int64_t)(o1 + i) * b + o + j] : 0.0;
+        Pb[0][i][j] = (i < tb1 && j < tbk) ? p.D0[(int64_t)(o1 + i) * b + o + j] : 0.0;
         S[i][j] = (i < tb1 && j <= i) ? p.D0[(int64_t)(o1 + i) * b + o1 + j] : 0.0;
       }
       __syncthreads();
@@ -861,7 +898,7 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
         const int i = e / T, j = e % T;
         if (j <= i && i < tb1) {
           double acc = 0.0;
-          for (int c = 0; c < tbk; ++c) acc = fma(P[i][c], P[j][c], acc);
+          for (int c = 0; c < tbk; ++c) acc = fma(Pb[0][i][c], Pb[0][j][c], acc);
           S[i][j] -= acc;
         }
       }
@@ -872,28 +909,90 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
         if (i < tb1 && j < tb1) p.D0[(int64_t)(o1 + i) * b + o1 + j] = S[i][j];
       }
       if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
-    } else {
-      const long long ntiles = (long long)m * (m + 1) / 2;
-      const int workers = look ? G - 1 : G, wid = look ? bid - 1 : bid;
-      for (long long t = (look ? 1 : 0) + wid; t < ntiles; t += workers) {
-        int rr = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((long long)(rr + 1) * (rr + 2) / 2 <= t) ++rr;
-        while ((long long)rr * (rr + 1) / 2 > t) --rr;
-        const int cc = (int)(t - (long long)rr * (rr + 1) / 2);
-        const int r = k + 1 + rr, c = k + 1 + cc;
+    }
+    {
+      // Lower triangle over the extended tiles k+1..E-1 (without (k+1, k+1) under
+      // look-ahead). CTAs take tiles from a per-step counter (CTA 0 joins after
+      // its look-ahead), so the SMs that share their FP64 pipe with a slower
+      // neighbour take fewer; the tile pair after the current one is already in
+      // flight (cp.async) and the index after that is fetched during the DMMAs.
+      const int first = look ? 1 : 0;
+      const int nitems = m * (m + 1) / 2 - first;
+      int* ctr = p.ctr + k;
+      auto decode = [&](int t, int& r, int& c) {
+        const int u = t + first, rr = tri_row(u);
+        r = k + 1 + rr;
+        c = k + 1 + (u - rr * (rr + 1) / 2);
+      };
+      auto issue = [&](int t, int bf) {
+        int r, c;
+        decode(t, r, c);
         const int rb = ext_rows(p, r), cb = ext_rows(p, c);
-        int64_t ldr, ldq, ldc;
+        int64_t ldr, ldq;
         const double* Lr = ext_tile(p, r, k, ldr);
         const double* Lc = ext_tile(p, c, k, ldq);
-        double* C = ext_tile(p, r, c, ldc);
-        __syncthreads();
         for (int e = tid; e < T * T; e += blockDim.x) {
           const int i = e / T, j = e % T;
-          P[i][j] = (i < rb && j < tbk) ? Lr[(int64_t)i * ldr + j] : 0.0;
-          Q[i][j] = (i < cb && j < tbk) ? Lc[(int64_t)i * ldq + j] : 0.0;
+          const bool pr = i < rb && j < tbk, pc = i < cb && j < tbk;
+          cp_async8(&Pb[bf][i][j], pr ? Lr + (int64_t)i * ldr + j : Lr, pr);
+          cp_async8(&Qb[bf][i][j], pc ? Lc + (int64_t)i * ldq + j : Lc, pc);
         }
+        cp_async_commit();
+      };
+      __syncthreads();  // s_next of the previous step has been read by every thread
+      if (tid == 0) {
+        s_next[0] = atomicAdd(ctr, 1);
+        s_next[1] = atomicAdd(ctr, 1);
+      }
+      __syncthreads();
+      int t = s_next[0], t1 = s_next[1], bf = 0;
+      if (t < nitems) issue(t, 0);
+      if (t1 < nitems) issue(t1, 1);
+      while (t < nitems) {
+        if (t1 < nitems)
+          cp_async_wait<1>();
+        else
+          cp_async_wait<0>();
         __syncthreads();
-        coop_tile_update(C, ldc, rb, cb, P, Q, T);
+        int t2 = 0;
+        if (tid == 0) t2 = atomicAdd(ctr, 1);  // in flight during the DMMAs
+        int r, c;
+        decode(t, r, c);
+        const int rb = ext_rows(p, r), cb = ext_rows(p, c);
+        int64_t ldc;
+        double* C = ext_tile(p, r, c, ldc);
+        const int row = wm + gq;
+        if (wm < rb && wn < cb) {  // warp-uniform
+          double cold[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+          double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const int col = wn + ni * 8 + 2 * tq + j;
+              if (row < rb && col < cb) cold[ni][j] = C[(int64_t)row * ldc + col];
+            }
+#pragma unroll
+          for (int ks = 0; ks < T; ks += 4) {
+            const double av = Pb[bf][row][ks + tq];
+            dmma_8x8x4(acc[0], av, Qb[bf][wn + gq][ks + tq]);
+            dmma_8x8x4(acc[1], av, Qb[bf][wn + 8 + gq][ks + tq]);
+          }
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const int col = wn + ni * 8 + 2 * tq + j;
+              if (row < rb && col < cb) C[(int64_t)row * ldc + col] = cold[ni][j] - acc[ni][j];
+            }
+        }
+        if (tid == 0) s_next[0] = t2;
+        __syncthreads();  // the buffer is consumed and s_next[0] is published
+        t2 = s_next[0];
+        if (t2 < nitems) issue(t2, bf);
+        t = t1;
+        t1 = t2;
+        bf ^= 1;
       }
     }
     grid_barrier(p.bar, G, gen);
@@ -936,12 +1035,14 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
   p.row0 = info_row0;
   p.bar = (CoopBar*)scratch;
   p.rdiag = (double*)((char*)scratch + 256);
+  p.ctr = (int*)((char*)scratch + 1024);
+  if (p.nt > kStepMaxTiles) return cudaErrorInvalidValue;
   if (b < 1 || a < 0 || (next && (!Lw || !D1 || (a > 0 && !Ar1))) || (a > 0 && (!Ar0 || !tip)))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(CoopBar), s);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 1024 + kStepMaxTiles * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int G = step_grid();
-  if (G < 1) return cudaErrorInvalidConfiguration;
+  if (G < 2) return cudaErrorInvalidConfiguration;
   void* args[] = {&p};
   TimedLaunch tl(K_FACTOR_STEP, timing_on() ? step_flops(b, a, p.next) : 0.0, s);
   return cudaLaunchCooperativeKernel((void*)factor_step_kernel, dim3(G), dim3(256), args, 0, s);
