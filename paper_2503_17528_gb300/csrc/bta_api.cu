@@ -42,7 +42,7 @@ struct SelinvWs { double *Linv, *G, *H, *LtInv; void* tc; size_t tc_bytes; };
 
 extern int g_prec;
 size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch, int prec);
-struct SolveWs { double* partial; };
+struct SolveWs { double* partial; double* dinv; };
 struct LogdetWs { double* partial; };
 
 size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o, int prec) {
@@ -73,10 +73,10 @@ size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o, int prec
 }
 
 size_t solve_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, SolveWs* o) {
-  (void)b;
   Carver c(p);
   SolveWs w;
   w.partial = c.take((size_t)(arrow_chunks(n) * a * R + 1));
+  w.dinv = c.take((size_t)(n * ((b + T - 1) / T) * T * T));
   if (o) *o = w;
   return c.off;
 }
@@ -311,11 +311,14 @@ int solve_impl(int64_t n, int64_t b, int64_t a, const double* diag, const double
   const int B = (int)b, Rr = (int)R;
   const int64_t bb = b * b, bR = b * R;
   double* rn = rhs + n * bR;
+  // Inverses of the T x T diagonal tiles of every L_ii, shared by both sweeps.
+  const int64_t dstride = ((b + T - 1) / T) * T * T;
+  BTA_TRY(tile_inverses(diag, b, bb, (int)n, B, w.dinv, s));
   for (int64_t i = 0; i < n; ++i) {
     if (i > 0)
       BTA_TRY(gemv_multi(lower + (i - 1) * bb, b, OP_N, B, B, rhs + (i - 1) * bR, R,
                          rhs + i * bR, R, Rr, -1.0, s));
-    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, false, s));
+    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, false, s, w.dinv + i * dstride));
   }
   if (a > 0) {
     BTA_TRY(arrow_gather(arrow, n, b, a, rhs, Rr, w.partial, arrow_chunks(n), rn, s));
@@ -327,7 +330,7 @@ int solve_impl(int64_t n, int64_t b, int64_t a, const double* diag, const double
     if (i + 1 < n)
       BTA_TRY(gemv_multi(lower + i * bb, b, OP_T, B, B, rhs + (i + 1) * bR, R, rhs + i * bR, R,
                          Rr, -1.0, s));
-    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, true, s));
+    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, true, s, w.dinv + i * dstride));
   }
   return 0;
 }

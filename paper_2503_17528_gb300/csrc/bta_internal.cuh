@@ -59,11 +59,14 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          cudaStream_t s);
 // Cooperative single-launch POTRF of one nrow x nrow block (nrow >= 64 pays);
 // scratch: coop_scratch_bytes, 256-byte aligned.
-constexpr size_t kCoopScratch = 256 + 2 * T * T * sizeof(double);
-// Largest tile count per block order of the fused factor step (b <= 32768); its
-// per-launch flags sit at byte 1024 of the same scratch.
+constexpr size_t kCoopScratch = 32768;
+// Largest tile counts of the fused factor step (b, a <= 32768): tiles per block
+// order and extended rows (two blocks plus the arrowhead). Its per-launch
+// counters and flags sit from byte 1016 of the same scratch.
 constexpr int kStepMaxTiles = 1024;
-static_assert(1024 + kStepMaxTiles * sizeof(int) <= kCoopScratch, "step scratch");
+constexpr int kStepMaxExtTiles = 3 * 1024;
+static_assert(1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int) <= kCoopScratch,
+              "step scratch");
 cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
                        cudaStream_t s);
 // One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}
@@ -102,8 +105,15 @@ cudaError_t logdet_combine(const double* p1, int64_t n1, const double* p2, int64
 cudaError_t axpy_f64(int64_t n, double alpha, const double* x, double* y, cudaStream_t s);
 
 // Solve pieces (rhs row-major [rows][R]).
+// Inverses of the T x T diagonal tiles of `count` lower-triangular blocks
+// (order nrow, stride sl), packed as D[block][tile][T][T].
+cudaError_t tile_inverses(const double* L, int64_t ld, int64_t sl, int count, int nrow,
+                          double* D, cudaStream_t s);
+// x <- L^{-1} x (trans: L^{-T} x) by one thread-block cluster; Dinv (optional):
+// L's packed diagonal-tile inverses, which replace the per-tile substitution.
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x,
-                       int64_t ldx, int R, bool trans, cudaStream_t s);
+                       int64_t ldx, int R, bool trans, cudaStream_t s,
+                       const double* Dinv = nullptr);
 // x[M][R] += alpha * op(A) * y[K][R], op(A) is M x K.
 cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K,
                        const double* y, int64_t ldy, double* x, int64_t ldx,

@@ -64,7 +64,27 @@ __device__ __forceinline__ double scale_by(double v, double alpha) {
   return alpha * v;
 }
 
-__global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+}
+
+// Load of a double from the shared memory of CTA `rank` of this cluster, at the
+// address that `local` has in this CTA.
+__device__ __forceinline__ double ld_dsmem(const double* local, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+  unsigned ra;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];\n" : "=d"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// ksplit > 1: the CTAs of a cluster of ksplit share one output tile and split
+// its k-chunks (concatenated over the terms) into contiguous ranges; rank 0 adds
+// the partial tiles in rank order from distributed shared memory (the result is
+// deterministic for a given ksplit) and writes C.
+__global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g, int ksplit) {
   __shared__ double As[T][T + 1];  // [m][k]
   __shared__ double Bs[T][T + 1];  // [k][n]
   const int tilesN = (g.N + T - 1) / T;
@@ -76,6 +96,11 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
   const long long per_batch = tri_enum ? (long long)tilesM * (tilesM + 1) / 2
                                        : (long long)tilesM * tilesN;
   long long bid = blockIdx.x;
+  unsigned part = 0;
+  if (ksplit > 1) {
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(part));
+    bid /= ksplit;
+  }
   const long long tidx = bid % per_batch;
   bid /= per_batch;
   int tm, tn;
@@ -105,16 +130,33 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
-  for (int ti = 0; ti < g.nterms; ++ti) {
-    const GemmTerm& t = g.t[ti];
-    const double* A = t.A + (int64_t)z1 * t.sA1 + (int64_t)z2 * t.sA2;
-    const double* B = t.B + (int64_t)z1 * t.sB1 + (int64_t)z2 * t.sB2;
-    int kb = 0, ke = t.K;
+  auto krange = [&](const GemmTerm& t, int& kb, int& ke) {
+    kb = 0;
+    ke = t.K;
     if (t.triA == TRI_LOWER) ke = min(ke, m0 + T);
     if (t.triA == TRI_UPPER) kb = max(kb, m0);
     if (t.triB == TRI_LOWER) kb = max(kb, n0);
     if (t.triB == TRI_UPPER) ke = min(ke, n0 + T);
-    for (int k0 = kb; k0 < ke; k0 += T) {
+  };
+  int c_lo = 0, c_hi = 0x7fffffff, cidx = 0;
+  if (ksplit > 1) {
+    int nch = 0;
+    for (int ti = 0; ti < g.nterms; ++ti) {
+      int kb, ke;
+      krange(g.t[ti], kb, ke);
+      if (ke > kb) nch += (ke - kb + T - 1) / T;
+    }
+    c_lo = (int)((long long)part * nch / ksplit);
+    c_hi = (int)((long long)(part + 1) * nch / ksplit);
+  }
+  for (int ti = 0; ti < g.nterms; ++ti) {
+    const GemmTerm& t = g.t[ti];
+    const double* A = t.A + (int64_t)z1 * t.sA1 + (int64_t)z2 * t.sA2;
+    const double* B = t.B + (int64_t)z1 * t.sB1 + (int64_t)z2 * t.sB2;
+    int kb, ke;
+    krange(t, kb, ke);
+    for (int k0 = kb; k0 < ke; k0 += T, ++cidx) {
+      if (cidx < c_lo || cidx >= c_hi) continue;  // uniform over the CTA
       for (int e = tid; e < T * T; e += 128) {
         int i, kk;
         double v = 0.0;
@@ -159,6 +201,29 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g) {
       }
       __syncthreads();
     }
+  }
+
+  if (ksplit > 1) {
+    double* red = &As[0][0];  // 8 partial sums per thread
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) red[((i * 2 + j) * 2 + h) * 128 + tid] = acc[i][j][h];
+    cluster_sync_all();
+    if (part == 0) {
+      for (int q = 1; q < ksplit; ++q)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              acc[i][j][h] += ld_dsmem(red + ((i * 2 + j) * 2 + h) * 128 + tid, (unsigned)q);
+    }
+    cluster_sync_all();  // the partial tiles stay readable until rank 0 is done
+    if (part != 0) return;
   }
 
   double* C = g.C + (int64_t)z1 * g.sC1 + (int64_t)z2 * g.sC2;
@@ -283,6 +348,41 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(GemmArgs g) {
   }
 }
 
+// Split of each output tile's k-chunks over a cluster: launches that fill less
+// than a wave of CTA slots leave the SMs unevenly loaded (every resident CTA
+// shares its SM's FP64 pipe), so the split is chosen to even out the CTAs per SM
+// (mean over max CTAs per SM) while staying within one wave and keeping at least
+// 4 chunks per part. (Splitting past a wave measured slower: 1024 tiles of a
+// 1024 x 1024 x 1032 product took 2.21 ms split 4-way against 2.17 ms unsplit.)
+static int gemm_ksplit(long long ctas, int kchunks) {
+  static int sms = 0, per_sm = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_f64_kernel, 128, 0);
+    if (sms < 1) sms = 1;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const long long slots = (long long)sms * per_sm;
+  if (ctas >= slots) return 1;
+  auto eff = [&](long long n) {
+    const double per = (double)n / sms;
+    return per / std::ceil(per);
+  };
+  int best = 1;
+  double be = eff(ctas);
+  for (int k = 2; k <= 4; k *= 2) {
+    if (kchunks / k < 4 || ctas * k > slots) break;
+    const double e = eff(ctas * k);
+    if (e > be + 0.01) {
+      be = e;
+      best = k;
+    }
+  }
+  return best;
+}
+
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
   if (g.M <= kSkinnyMaxM && g.N >= 64) {
@@ -295,10 +395,27 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
   const long long tm = (g.M + T - 1) / T, tn = (g.N + T - 1) / T;
   const long long tiles = (g.lowerC && g.M == g.N) ? tm * (tm + 1) / 2 : tm * tn;
   const long long grid = tiles * g.nb1 * g.nb2;
-  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  int kch = 0;
+  for (int i = 0; i < g.nterms; ++i) kch += (g.t[i].K + T - 1) / T;
+  const int ks = gemm_ksplit(grid, kch);
+  if (grid * ks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   TimedLaunch tl(K_GEMM, timing_on() ? gemm_alg_flops(g) : 0.0, s);
-  gemm_f64_kernel<<<(unsigned)grid, 128, 0, s>>>(g);
-  return cudaGetLastError();
+  if (ks == 1) {
+    gemm_f64_kernel<<<(unsigned)grid, 128, 0, s>>>(g, 1);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(grid * ks));
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_f64_kernel, g, ks);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,19 +531,18 @@ __global__ void mirror_kernel(double* A, int64_t ld, int64_t sb, int nrow) {
   }
 }
 
-// Inverse of each diagonal tile of lower-triangular blocks into Linv.
-__global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t ldl, int64_t sl,
-                                                       double* Li, int64_t ldi, int64_t si,
-                                                       int nrow) {
+// Inverse of one diagonal tile (order tb <= T) of a lower-triangular block:
+// Lb points at the tile's (0,0); the inverse goes to Xb (leading dimension ldx),
+// zero above the diagonal.
+__device__ __forceinline__ void tile_inv_body(const double* Lb, int64_t ldl, double* Xb,
+                                              int64_t ldx, int tb) {
   __shared__ double Ls[T][T + 1];
   __shared__ double X[T][T + 1];
   __shared__ double rd[T];
-  const int o = blockIdx.x * T, tb = min(T, nrow - o), tid = threadIdx.x;
-  const double* Lb = L + (int64_t)blockIdx.y * sl;
-  double* Xb = Li + (int64_t)blockIdx.y * si;
+  const int tid = threadIdx.x;
   for (int e = tid; e < T * T; e += blockDim.x) {
     const int i = e / T, j = e % T;
-    Ls[i][j] = (i < tb && j <= i) ? Lb[(int64_t)(o + i) * ldl + o + j] : 0.0;
+    Ls[i][j] = (i < tb && j <= i) ? Lb[(int64_t)i * ldl + j] : 0.0;
     X[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -445,8 +561,40 @@ __global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t 
   }
   for (int e = tid; e < tb * tb; e += blockDim.x) {
     const int i = e / tb, j = e % tb;
-    Xb[(int64_t)(o + i) * ldi + o + j] = (j <= i) ? X[i][j] : 0.0;
+    Xb[(int64_t)i * ldx + j] = (j <= i) ? X[i][j] : 0.0;
   }
+}
+
+// Inverse of each diagonal tile of lower-triangular blocks into the same
+// positions of Linv (grid: tiles x blocks).
+__global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t ldl, int64_t sl,
+                                                       double* Li, int64_t ldi, int64_t si,
+                                                       int nrow) {
+  const int o = blockIdx.x * T, tb = min(T, nrow - o);
+  tile_inv_body(L + (int64_t)blockIdx.y * sl + (int64_t)o * ldl + o, ldl,
+                Li + (int64_t)blockIdx.y * si + (int64_t)o * ldi + o, ldi, tb);
+}
+
+// The same inverses packed as [block][tile][T][T] (entries beyond a ragged last
+// tile's order are left unwritten).
+__global__ void __launch_bounds__(256) tile_inv_packed_kernel(const double* L, int64_t ld,
+                                                              int64_t sl, double* D, int nrow) {
+  const int nt = (nrow + T - 1) / T, o = blockIdx.x * T, tb = min(T, nrow - o);
+  tile_inv_body(L + (int64_t)blockIdx.y * sl + (int64_t)o * ld + o, ld,
+                D + ((int64_t)blockIdx.y * nt + blockIdx.x) * T * T, T, tb);
+}
+
+cudaError_t tile_inverses(const double* L, int64_t ld, int64_t sl, int count, int nrow,
+                          double* D, cudaStream_t s) {
+  if (count <= 0 || nrow <= 0) return cudaSuccess;
+  const int nt = (nrow + T - 1) / T;
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = min(65535, count - c0);
+    TimedLaunch tl(K_TILE_INV, 0.0, s);
+    tile_inv_packed_kernel<<<dim3(nt, cnt), 256, 0, s>>>(L + (int64_t)c0 * sl, ld, sl,
+                                                         D + (int64_t)c0 * nt * T * T, nrow);
+  }
+  return cudaGetLastError();
 }
 
 static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
@@ -729,6 +877,8 @@ cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, voi
 // same tile sweep, so the latency-bound tile steps of the POTRF overlap with
 // the bulk of the step's work.
 // ---------------------------------------------------------------------------
+constexpr int kStepThreads = 256;
+
 struct StepArgs {
   double* D0;   // A_ii (b x b): L_ii on return, strict upper triangle zeroed
   double* Lw;   // A_{i+1,i} (b x b): L_{i+1,i}; unused when next == 0
@@ -740,7 +890,11 @@ struct StepArgs {
   long long row0;  // 1-based global row of block i's first row, minus one
   CoopBar* bar;
   double* rdiag;  // [2][T]: 1 / L_jj of the current diagonal tile (by step parity)
-  int* ctr;       // [nt]: tiles taken so far in step k (zeroed per launch)
+  int* ctr;       // [nt]: items taken so far in step k
+  int* lflag;     // = k + 1 once tile (k+1, k+1) is factored in step k
+  int* colflag;   // [extended rows]: = k + 1 once tile (r, k+1) has its step-k update
+                  // (all three zeroed per launch)
+  int* smid0;     // SM of CTA 0
 };
 
 // Group of an extended tile row (0: block i, 1: block i+1, 2: arrow) and its
@@ -820,13 +974,39 @@ __device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*L
   }
 }
 
-__global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
-  __shared__ double S[T][T + 1];  // CTA 0: the look-ahead tile
-  __shared__ double Lt[T][T + 1]; // L_kk for the panel slices
+// Bounded wait until *flag >= v (a flag another CTA of the same cooperative
+// launch raises); on timeout the error word is set and the CTA goes on.
+__device__ __forceinline__ void wait_flag_ge(const int* flag, int v) {
+  if (threadIdx.x == 0) {
+    unsigned polls = 0;
+    while (atomicAdd((int*)flag, 0) < v) {
+      if (++polls > (1u << 24)) {
+        atomicExch(&g_wait_error, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Publishes *flag = v after this CTA's preceding global writes (call after a
+// __syncthreads that follows them).
+__device__ __forceinline__ void raise_flag(int* flag, int v) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flag, v);
+  }
+}
+
+__global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p) {
+  __shared__ double S[T][T + 1];   // look-ahead tile (CTA 0) or a panel slice
+  __shared__ double Lt[T][T + 1];  // the diagonal factor the panel slices are solved with
   __shared__ double Pb[2][T][T + 1];
   __shared__ double Qb[2][T][T + 1];
   __shared__ double rd[T];
-  __shared__ int s_next[2];
+  __shared__ int s_next;
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
   const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
   const int wm = (warp >> 1) * 8, wn = (warp & 1) * 16;  // this warp's 8 x 16 part of a tile
@@ -834,7 +1014,11 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
   const int64_t b = p.b;
   unsigned gen = 0;
 
-  if (bid == 0) {  // step 0's diagonal tile
+  // Prologue: tile (0, 0), then the panel tiles of column 0.
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  if (bid == 0) {
+    if (tid == 0) *p.smid0 = (int)smid;
     const int tb = min(T, p.b);
     for (int e = tid; e < T * T; e += blockDim.x) {
       const int i = e / T, j = e % T;
@@ -849,45 +1033,52 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
     if (tid < T) p.rdiag[tid] = rd[tid];
   }
   grid_barrier(p.bar, G, gen);
-  for (int k = 0; k < nt; ++k) {
-    const int o = k * T, tbk = min(T, p.b - o);
-    const double* rdk = p.rdiag + (k & 1) * T;
-    const double* Lkk = p.D0 + (int64_t)o * b + o;
-    // A. panel: row slices of the tiles below (k, k), X L_kk^T = A(r, k); the
-    // slices are as short as one round over the grid allows (8, 16 or 32 rows).
-    const int below = E - k - 1;
+  // A CTA on CTA 0's SM takes no tiles during the look-ahead, which then runs
+  // without contention on that SM's FP64 pipe.
+  const bool beside0 = bid != 0 && (int)smid == *(volatile int*)p.smid0;
+  {
+    const int below = E - 1, tb0 = min(T, p.b);
     const int per = 4 * below <= G ? 4 : (2 * below <= G ? 2 : 1), sh = T / per;
-    const int nslices = per * below;
     bool loaded = false;
-    for (int sl = bid; sl < nslices; sl += G) {
-      const int r = k + 1 + sl / per, rs = (sl % per) * sh;
+    for (int sl = bid; sl < per * below; sl += G) {
+      const int r = 1 + sl / per, rs = (sl % per) * sh;
       const int rows = min(sh, ext_rows(p, r) - rs);
       if (rows <= 0) continue;  // uniform over the CTA
       int64_t ldx;
-      double* X = ext_tile(p, r, k, ldx);
+      double* X = ext_tile(p, r, 0, ldx);
       X += (int64_t)rs * ldx;
       __syncthreads();
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, j = e % T;
-        if (!loaded) Lt[i][j] = (i < tbk && j <= i) ? Lkk[(int64_t)i * b + j] : 0.0;
-        S[i][j] = (i < rows && j < tbk) ? X[(int64_t)i * ldx + j] : 0.0;
+        if (!loaded) Lt[i][j] = (i < tb0 && j <= i) ? p.D0[(int64_t)i * b + j] : 0.0;
+        S[i][j] = (i < rows && j < tb0) ? X[(int64_t)i * ldx + j] : 0.0;
       }
-      if (!loaded && tid < T) rd[tid] = rdk[tid];
+      if (!loaded && tid < T) rd[tid] = p.rdiag[tid];
       loaded = true;
       __syncthreads();
-      panel_solve(S, Lt, rd, rows, tbk);
-      for (int e = tid; e < rows * tbk; e += blockDim.x) {
-        const int i = e / tbk, c = e % tbk;
+      panel_solve(S, Lt, rd, rows, tb0);
+      for (int e = tid; e < rows * tb0; e += blockDim.x) {
+        const int i = e / tb0, c = e % tb0;
         X[(int64_t)i * ldx + c] = S[i][c];
       }
     }
-    grid_barrier(p.bar, G, gen);
+  }
+  grid_barrier(p.bar, G, gen);
+
+  // Tile step k. Work items, taken in order from a per-step counter:
+  //   1. the tiles (r, k+1), r > k+1: -= L(r,k) L(k+1,k)^T, then flagged;
+  //   2. the other trailing tiles (r, c), r >= c > k+1 (or >= k+1 without look-ahead);
+  //   3. the panel slices of column k+1 (X L_{k+1,k+1}^T = A(r, k+1)), each once
+  //      its tile is flagged and CTA 0 has factored (k+1, k+1).
+  // CTA 0 first factors tile (k+1, k+1) (after its step-k update) and then joins.
+  // Every item waits only on items earlier in the order, held by running CTAs.
+  for (int k = 0; k < nt; ++k) {
     const int m = E - k - 1;  // extended tiles below k
     if (m == 0) break;        // last block without arrowhead: nothing trails the last panel
-    // B. trailing updates of step k; CTA 0 takes tile (k+1, k+1) and factors it.
+    const int o = k * T, tbk = min(T, p.b - o);
     const bool look = k + 1 < nt;
+    const int o1 = o + T, tb1 = look ? min(T, p.b - o1) : 0;
     if (look && bid == 0) {
-      const int o1 = o + T, tb1 = min(T, p.b - o1);
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, j = e % T;
         Pb[0][i][j] = (i < tb1 && j < tbk) ? p.D0[(int64_t)(o1 + i) * b + o + j] : 0.0;
@@ -909,22 +1100,32 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
         if (i < tb1 && j < tb1) p.D0[(int64_t)(o1 + i) * b + o1 + j] = S[i][j];
       }
       if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
+      __syncthreads();
+      raise_flag(p.lflag, k + 1);
     }
-    {
-      // Lower triangle over the extended tiles k+1..E-1 (without (k+1, k+1) under
-      // look-ahead). CTAs take tiles from a per-step counter (CTA 0 joins after
-      // its look-ahead), so the SMs that share their FP64 pipe with a slower
-      // neighbour take fewer; the tile pair after the current one is already in
-      // flight (cp.async) and the index after that is fetched during the DMMAs.
-      const int first = look ? 1 : 0;
-      const int nitems = m * (m + 1) / 2 - first;
-      int* ctr = p.ctr + k;
-      auto decode = [&](int t, int& r, int& c) {
-        const int u = t + first, rr = tri_row(u);
-        r = k + 1 + rr;
-        c = k + 1 + (u - rr * (rr + 1) / 2);
-      };
-      auto issue = [&](int t, int bf) {
+    if (look && beside0) wait_flag_ge(p.lflag, k + 1);
+    const int ncol = look ? m - 1 : 0;                 // category 1
+    const int tri0 = look ? k + 2 : k + 1, tm = E - tri0;
+    const int nupd = ncol + tm * (tm + 1) / 2;          // categories 1 + 2
+    const int per = 2, sh = T / per;                    // category 3: 16-row slices
+    const int nitems = nupd + (look ? per * (m - 1) : 0);
+    int* ctr = p.ctr + k;
+    auto decode = [&](int t, int& r, int& c) {
+      if (t < ncol) {
+        r = k + 2 + t;
+        c = k + 1;
+      } else if (t < nupd) {
+        const int u = t - ncol, rr = tri_row(u);
+        r = tri0 + rr;
+        c = tri0 + (u - rr * (rr + 1) / 2);
+      } else {
+        const int sidx = t - nupd;
+        r = k + 2 + sidx / per;
+        c = (sidx % per) * sh;  // row offset of the slice inside its tile
+      }
+    };
+    auto issue = [&](int t, int bf) {
+      if (t < nupd) {
         int r, c;
         decode(t, r, c);
         const int rb = ext_rows(p, r), cb = ext_rows(p, c);
@@ -937,27 +1138,31 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
           cp_async8(&Pb[bf][i][j], pr ? Lr + (int64_t)i * ldr + j : Lr, pr);
           cp_async8(&Qb[bf][i][j], pc ? Lc + (int64_t)i * ldq + j : Lc, pc);
         }
-        cp_async_commit();
-      };
-      __syncthreads();  // s_next of the previous step has been read by every thread
-      if (tid == 0) {
-        s_next[0] = atomicAdd(ctr, 1);
-        s_next[1] = atomicAdd(ctr, 1);
       }
+      cp_async_commit();  // (an empty group for a slice keeps the group count in step)
+    };
+    __syncthreads();
+    if (tid == 0) s_next = atomicAdd(ctr, 1);
+    __syncthreads();
+    int t = s_next;
+    __syncthreads();
+    if (tid == 0) s_next = atomicAdd(ctr, 1);
+    __syncthreads();
+    int t1 = s_next, bf = 0;
+    bool have_lt = false;
+    if (t < nitems) issue(t, 0);
+    if (t1 < nitems) issue(t1, 1);
+    while (t < nitems) {
+      if (t1 < nitems)
+        cp_async_wait<1>();
+      else
+        cp_async_wait<0>();
       __syncthreads();
-      int t = s_next[0], t1 = s_next[1], bf = 0;
-      if (t < nitems) issue(t, 0);
-      if (t1 < nitems) issue(t1, 1);
-      while (t < nitems) {
-        if (t1 < nitems)
-          cp_async_wait<1>();
-        else
-          cp_async_wait<0>();
-        __syncthreads();
-        int t2 = 0;
-        if (tid == 0) t2 = atomicAdd(ctr, 1);  // in flight during the DMMAs
-        int r, c;
-        decode(t, r, c);
+      int t2 = 0;
+      if (tid == 0) t2 = atomicAdd(ctr, 1);  // in flight during the item
+      int r, c;
+      decode(t, r, c);
+      if (t < nupd) {
         const int rb = ext_rows(p, r), cb = ext_rows(p, c);
         int64_t ldc;
         double* C = ext_tile(p, r, c, ldc);
@@ -986,14 +1191,38 @@ __global__ void __launch_bounds__(256, 2) factor_step_kernel(StepArgs p) {
               if (row < rb && col < cb) C[(int64_t)row * ldc + col] = cold[ni][j] - acc[ni][j];
             }
         }
-        if (tid == 0) s_next[0] = t2;
-        __syncthreads();  // the buffer is consumed and s_next[0] is published
-        t2 = s_next[0];
-        if (t2 < nitems) issue(t2, bf);
-        t = t1;
-        t1 = t2;
-        bf ^= 1;
+      } else {
+        // Panel slice of tile (r, k+1), rows c .. c+sh-1.
+        const int rows = min(sh, ext_rows(p, r) - c);
+        if (rows > 0) {  // uniform over the CTA
+          if (!have_lt) wait_flag_ge(p.lflag, k + 1);
+          wait_flag_ge(p.colflag + r, k + 1);
+          int64_t ldx;
+          double* X = ext_tile(p, r, k + 1, ldx);
+          X += (int64_t)c * ldx;
+          for (int e = tid; e < T * T; e += blockDim.x) {
+            const int i = e / T, j = e % T;
+            if (!have_lt) Lt[i][j] = (i < tb1 && j <= i) ? p.D0[(int64_t)(o1 + i) * b + o1 + j] : 0.0;
+            if (i < sh) S[i][j] = (i < rows && j < tb1) ? X[(int64_t)i * ldx + j] : 0.0;
+          }
+          if (!have_lt && tid < T) rd[tid] = p.rdiag[((k + 1) & 1) * T + tid];
+          have_lt = true;
+          __syncthreads();
+          panel_solve(S, Lt, rd, rows, tb1);
+          for (int e = tid; e < rows * tb1; e += blockDim.x) {
+            const int i = e / tb1, j = e % tb1;
+            X[(int64_t)i * ldx + j] = S[i][j];
+          }
+        }
       }
+      if (tid == 0) s_next = t2;
+      __syncthreads();  // the buffer is consumed, stores are done, s_next is published
+      if (t < ncol) raise_flag(p.colflag + r, k + 1);
+      t2 = s_next;
+      if (t2 < nitems) issue(t2, bf);
+      t = t1;
+      t1 = t2;
+      bf ^= 1;
     }
     grid_barrier(p.bar, G, gen);
   }
@@ -1010,9 +1239,10 @@ static int step_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_step_kernel, 256, 0);
-    // Two CTAs per SM: one CTA's tile loads overlap the other's DMMA work.
-    cached = per >= 2 ? 2 * sms : (per >= 1 ? sms : 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_step_kernel, kStepThreads, 0);
+    // Several CTAs per SM: one CTA's loads, stores and barriers overlap the
+    // others' DMMA work on the SM's FP64 pipe.
+    cached = std::min(per, 2) * sms;
   }
   return cached;
 }
@@ -1035,17 +1265,22 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
   p.row0 = info_row0;
   p.bar = (CoopBar*)scratch;
   p.rdiag = (double*)((char*)scratch + 256);
+  p.lflag = (int*)((char*)scratch + 1016);
+  p.smid0 = (int*)((char*)scratch + 1012);
   p.ctr = (int*)((char*)scratch + 1024);
-  if (p.nt > kStepMaxTiles) return cudaErrorInvalidValue;
+  p.colflag = p.ctr + kStepMaxTiles;
+  if (p.nt > kStepMaxTiles || 2 * p.nt + p.na > kStepMaxExtTiles) return cudaErrorInvalidValue;
   if (b < 1 || a < 0 || (next && (!Lw || !D1 || (a > 0 && !Ar1))) || (a > 0 && (!Ar0 || !tip)))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, 1024 + kStepMaxTiles * sizeof(int), s);
+  cudaError_t e =
+      cudaMemsetAsync(scratch, 0, 1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int G = step_grid();
   if (G < 2) return cudaErrorInvalidConfiguration;
   void* args[] = {&p};
   TimedLaunch tl(K_FACTOR_STEP, timing_on() ? step_flops(b, a, p.next) : 0.0, s);
-  return cudaLaunchCooperativeKernel((void*)factor_step_kernel, dim3(G), dim3(256), args, 0, s);
+  return cudaLaunchCooperativeKernel((void*)factor_step_kernel, dim3(G), dim3(kStepThreads), args,
+                                     0, s);
 }
 
 cudaError_t wait_error_read_reset(int* out) {
@@ -1249,11 +1484,6 @@ cudaError_t logdet_f64(const double* diag, int64_t n, int64_t b, const double* t
 // publishes it, and every CTA subtracts its contribution from the row tiles it
 // owns that are still unsolved. The owner of tile k+1 has applied every update
 // to that tile itself, so one barrier per tile step suffices.
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory");
-  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
-}
-
 constexpr int kTrsvPrefetch = 4;  // row tiles per CTA whose L tiles are prefetched into registers
 
 // L tile element for the update of row tile r by solved tile k: L(r,k) (forward)
@@ -1265,8 +1495,8 @@ __device__ __forceinline__ double trsv_tile_el(const double* L, int64_t ld, int 
 }
 
 __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
-                                                           double* x, int64_t ldx, int R,
-                                                           int trans) {
+                                                           const double* Dinv, double* x,
+                                                           int64_t ldx, int R, int trans) {
   __shared__ double Xk[T][65];
   __shared__ double Lk[T][T + 1];
   __shared__ double Ld[T][T + 1];
@@ -1302,7 +1532,35 @@ __global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int6
         }
       }
     }
-    if (owner) {
+    if (owner && Dinv) {
+      // x_k = L_kk^{-1} r_k (or L_kk^{-T} r_k) with the precomputed tile inverse:
+      // independent dot products instead of a sequential substitution.
+      const double* D = Dinv + (int64_t)k * T * T;
+      for (int e = tid; e < T * T; e += blockDim.x) Ld[e / T][e % T] = D[e];
+      for (int e = tid; e < tb * R; e += blockDim.x)
+        Xk[e / R][e % R] = x[(int64_t)(o + e / R) * ldx + e % R];
+      __syncthreads();
+      for (int e = tid; e < tb * R; e += blockDim.x) {
+        const int i = e / R, q = e % R;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (!trans) {
+          for (int j = 0; j <= i; j += 4) {
+            a0 = fma(Ld[i][j], Xk[j][q], a0);
+            if (j + 1 <= i) a1 = fma(Ld[i][j + 1], Xk[j + 1][q], a1);
+            if (j + 2 <= i) a2 = fma(Ld[i][j + 2], Xk[j + 2][q], a2);
+            if (j + 3 <= i) a3 = fma(Ld[i][j + 3], Xk[j + 3][q], a3);
+          }
+        } else {
+          for (int j = i; j < tb; j += 4) {
+            a0 = fma(Ld[j][i], Xk[j][q], a0);
+            if (j + 1 < tb) a1 = fma(Ld[j + 1][i], Xk[j + 1][q], a1);
+            if (j + 2 < tb) a2 = fma(Ld[j + 2][i], Xk[j + 2][q], a2);
+            if (j + 3 < tb) a3 = fma(Ld[j + 3][i], Xk[j + 3][q], a3);
+          }
+        }
+        x[(int64_t)(o + i) * ldx + q] = (a0 + a1) + (a2 + a3);
+      }
+    } else if (owner) {
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, c = e % T;
         Ld[i][c] = (i < tb && c <= i) ? L[(int64_t)(o + i) * ld + o + c] : 0.0;
@@ -1401,7 +1659,7 @@ static int trsv_cluster_size(cudaStream_t s) {
 }
 
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t ldx, int R,
-                       bool trans, cudaStream_t s) {
+                       bool trans, cudaStream_t s, const double* Dinv) {
   if (nrow <= 0) return cudaSuccess;
   if (R > 64) return cudaErrorInvalidValue;
   const int nt = (nrow + T - 1) / T;
@@ -1419,7 +1677,7 @@ cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, x, ldx, R, trans ? 1 : 0);
+  return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, Dinv, x, ldx, R, trans ? 1 : 0);
 }
 
 // x[M][R] += alpha * A[M][K] y[K][R]: one warp per row, lanes over k, fixed-order
