@@ -169,9 +169,9 @@ cudaError_t trtri_hook(const GemmArgs& g, void* ctx, cudaStream_t s) {
   return gemm_run(g, CLS_TRSM, ((HookCtx*)ctx)->tw, ((HookCtx*)ctx)->prec, s);
 }
 
-// Blocks of at least this order are factored by the single-launch cooperative
-// POTRF (one matrix at a time); smaller ones, and matrices of a batch running on
-// concurrent streams, use the panel-by-panel launches.
+// Blocks of at least this order are factored by the cooperative step kernel (one
+// matrix at a time); smaller ones, and matrices of a batch running on concurrent
+// streams, use the panel-by-panel launches.
 constexpr int64_t kCoopMinB = 128;
 
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
@@ -196,8 +196,9 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   }
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
-    if (coop && b >= kCoopMinB)
-      BTA_TRY(potrf_coop(Di, b, B, i * b, w.coop, s));
+    if (coop && b >= kCoopMinB)  // the fused step kernel on A_ii alone: one cooperative POTRF
+      BTA_TRY(factor_step_coop(Di, nullptr, nullptr, nullptr, nullptr, nullptr, B, 0, 0, i * b,
+                               w.coop, s));
     else
       BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
     HookCtx hc{tw, prec};

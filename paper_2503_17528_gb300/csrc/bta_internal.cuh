@@ -57,8 +57,7 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s);
 cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          long long info_row0, long long info_rstride,
                          cudaStream_t s);
-// Cooperative single-launch POTRF of one nrow x nrow block (nrow >= 64 pays);
-// scratch: coop_scratch_bytes, 256-byte aligned.
+// Scratch of the cooperative factor-step kernel, 256-byte aligned.
 constexpr size_t kCoopScratch = 32768;
 // Largest tile counts of the fused factor step (b, a <= 32768): tiles per block
 // order and extended rows (two blocks plus the arrowhead). Its per-launch
@@ -67,8 +66,6 @@ constexpr int kStepMaxTiles = 1024;
 constexpr int kStepMaxExtTiles = 3 * 1024;
 static_assert(1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int) <= kCoopScratch,
               "step scratch");
-cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
-                       cudaStream_t s);
 // One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}
 // and L_{n,i} in place, and the Schur updates of A_{i+1,i+1}, A_{n,i+1} and the
 // tip (lower tiles). next == 0 for the last block (Lw, D1, Ar1 unused); a == 0:

@@ -600,17 +600,10 @@ cudaError_t tile_inverses(const double* L, int64_t ld, int64_t sl, int count, in
 static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// Cooperative POTRF of one block: the whole right-looking tile Cholesky in one
-// launch whose CTAs are all resident (cooperative launch), separated by
-// bounded grid barriers. Per step k:
-//   A. every CTA takes 8-row slices of the panel tiles (r, k), r > k:
-//      L(r,k) = A(r,k) L_kk^{-T} with the explicit L_kk^{-1} (DMMA);
-//   B. CTA 0 applies the step-k update to tile (k+1, k+1) first, factors it and
-//      inverts the factor (look-ahead: the next step's serial work), while the
-//      other CTAs apply the step-k updates to every other trailing tile.
-// The grid barrier counts arrivals and releases a generation word; a wait that
-// exceeds its poll limit records the timeout and lets the CTA go on, so the
-// kernel always ends (the caller reads the flag with bta_tc_status).
+// Cooperative-launch building blocks. The grid barrier counts arrivals and
+// releases a generation word; a wait that exceeds its poll limit records the
+// timeout and lets the CTA go on, so a kernel always ends (the caller reads the
+// flag with bta_tc_status).
 // ---------------------------------------------------------------------------
 __device__ int g_wait_error;
 
@@ -644,220 +637,72 @@ __device__ __forceinline__ void grid_barrier(CoopBar* bar, unsigned nblocks, uns
   __syncthreads();
 }
 
+// Row of the lower-triangular index u (u = row (row + 1) / 2 + col, col <= row).
+__device__ __forceinline__ int tri_row(int u) {
+  int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= u) ++r;
+  while (r * (r + 1) / 2 > u) --r;
+  return r;
+}
+
+// Pivot of a tile Cholesky: L_jj = d y with y = 1 / sqrt(d); a non-positive
+// pivot is recorded (LAPACK-style row) and poisons the rest with NaN.
+__device__ __forceinline__ void pivot_of(double d, long long row, double& Ljj, double& y) {
+  if (!(d > 0.0)) {
+    record_failure(row);
+    d = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  y = rsqrt_newton(d);
+  Ljj = d * y;
+}
+
 // Shared-memory Cholesky of a tb x tb tile in S (lower part valid); returns with
-// S = L (zero above) and rd[j] = 1 / L_jj. Records a failed pivot.
+// S = L (zero above) and rd[j] = 1 / L_jj. Records a failed pivot. Phase j
+// applies pivot j to the trailing triangle from the unscaled column j
+// (S_ic -= S_ij S_cj rd_j^2) and scales column j-1, while thread 0 finishes
+// diagonal entry j+1 and computes the next pivot: the pivot chain runs one step
+// ahead of the updates, one barrier per pivot. Needs more than one warp (the
+// updates run on warps 1 and up).
 __device__ void coop_factor(double (*S)[T + 1], double* rd, int tb, long long row_base) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    double L0, y0;
+    pivot_of(S[0][0], row_base + 1, L0, y0);
+    S[0][0] = L0;
+    rd[0] = y0;
+  }
+  __syncthreads();
   for (int j = 0; j < tb; ++j) {
-    if (tid == 0) {
-      double d = S[j][j];
-      if (!(d > 0.0)) {
-        record_failure(row_base + j + 1);
-        d = __longlong_as_double(0x7ff8000000000000ll);
-      }
-      const double y = rsqrt_newton(d);
-      S[j][j] = d * y;
-      rd[j] = y;
-    }
-    __syncthreads();
     const double r = rd[j];
-    for (int i = j + 1 + tid; i < tb; i += blockDim.x) S[i][j] *= r;
-    __syncthreads();
-    const int w = tb - j - 1;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
+    if (tid == 0) {
+      if (j + 1 < tb) {
+        const double sj = S[j + 1][j] * r;
+        double L1, y1;
+        pivot_of(fma(-sj, sj, S[j + 1][j + 1]), row_base + j + 2, L1, y1);
+        S[j + 1][j + 1] = L1;
+        rd[j + 1] = y1;
+      }
+    } else if (tid >= 32) {
+      const double r2 = r * r;
+      const int w = tb - j - 1, nel = w * (w + 1) / 2;
+      for (int e = tid - 32; e < nel; e += nthr - 32) {
+        const int rr = tri_row(e), cc = e - rr * (rr + 1) / 2;
+        if (rr == 0) continue;  // (j+1, j+1): thread 0's
+        const int i = j + 1 + rr, c = j + 1 + cc;
+        S[i][c] = fma(-S[i][j] * S[c][j], r2, S[i][c]);
+      }
+    }
+    if (j > 0) {  // column j-1 is no longer read: scale it
+      const double rp = rd[j - 1];
+      for (int i = j + tid; i < tb; i += nthr) S[i][j - 1] *= rp;
     }
     __syncthreads();
   }
-  for (int e = tid; e < T * T; e += blockDim.x) {
+  for (int e = tid; e < T * T; e += nthr) {
     const int i = e / T, c = e % T;
     if (c > i) S[i][c] = 0.0;
   }
   __syncthreads();
-}
-
-// C(32 x 32, global) -= P Q^T with P, Q 32 x 32 tiles in shared memory; 8 warps,
-// each two 8 x 8 DMMA tiles of the output.
-__device__ __forceinline__ void coop_tile_update(double* C, int64_t ld, int rows, int cols,
-                                                 double (*P)[T + 1], double (*Q)[T + 1], int kb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int m0 = (warp >> 1) * 8, n0 = (warp & 1) * 16;
-  if (m0 >= rows || n0 >= cols) return;  // warp-uniform: nothing of this warp's part is stored
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int ks = 0; ks < kb; ks += 4) {
-    const double a = P[m0 + gq][ks + tq];
-    dmma_8x8x4(acc[0], a, Q[n0 + gq][ks + tq]);
-    dmma_8x8x4(acc[1], a, Q[n0 + 8 + gq][ks + tq]);
-  }
-#pragma unroll
-  for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = m0 + gq, c = n0 + ni * 8 + 2 * tq + j;
-      if (r < rows && c < cols) C[(int64_t)r * ld + c] -= acc[ni][j];
-    }
-}
-
-struct CoopArgs {
-  double* A;
-  int64_t ld;
-  int nrow;
-  long long row0;
-  CoopBar* bar;
-  double* rdiag;  // [2][T] scratch: 1 / L_jj of the current diagonal tile (by step parity)
-};
-
-__global__ void __launch_bounds__(256) potrf_coop_kernel(CoopArgs p) {
-  __shared__ double S[T][T + 1];
-  __shared__ double P[T][T + 1];
-  __shared__ double Q[T][T + 1];
-  __shared__ double rd[T];
-  const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
-  const int nt = (p.nrow + T - 1) / T;
-  unsigned gen = 0;
-  double* A = p.A;
-  const int64_t ld = p.ld;
-
-  auto tb_of = [&](int t) { return min(T, p.nrow - t * T); };
-  // Step 0's diagonal tile.
-  if (bid == 0) {
-    const int tb = tb_of(0);
-    for (int e = tid; e < T * T; e += blockDim.x) {
-      const int i = e / T, j = e % T;
-      S[i][j] = (i < tb && j <= i) ? A[(int64_t)i * ld + j] : 0.0;
-    }
-    __syncthreads();
-    coop_factor(S, rd, tb, p.row0);
-    for (int e = tid; e < T * T; e += blockDim.x) {
-      const int i = e / T, j = e % T;
-      if (i < tb && j < tb) A[(int64_t)i * ld + j] = S[i][j];
-    }
-    if (tid < T) p.rdiag[tid] = rd[tid];
-  }
-  grid_barrier(p.bar, G, gen);
-  for (int k = 0; k < nt; ++k) {
-    const int o = k * T, tbk = tb_of(k);
-    const double* rdk = p.rdiag + (k & 1) * T;
-    // A. panel: 8-row slices of tiles r > k solve X L_kk^T = A(r,k) by a column sweep.
-    const int nslices = (nt - k - 1) * 4;
-    for (int sl = bid; sl < nslices; sl += G) {
-      const int r = k + 1 + sl / 4, rs = (sl % 4) * 8;
-      const int ro = r * T + rs, rows = min(8, p.nrow - ro);
-      __syncthreads();
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        Q[i][j] = (i < tbk && j <= i) ? A[(int64_t)(o + i) * ld + o + j] : 0.0;  // L_kk
-        if (i < 8) P[i][j] = (i < rows && j < tbk) ? A[(int64_t)(ro + i) * ld + o + j] : 0.0;
-      }
-      if (tid < T) rd[tid] = rdk[tid];
-      __syncthreads();
-      for (int j = 0; j < tbk; ++j) {
-        if (tid < rows) P[tid][j] *= rd[j];
-        __syncthreads();
-        const int w = tbk - j - 1;
-        for (int e = tid; e < rows * w; e += blockDim.x) {
-          const int i = e / w, c = j + 1 + e % w;
-          P[i][c] -= P[i][j] * Q[c][j];
-        }
-        __syncthreads();
-      }
-      for (int e = tid; e < rows * tbk; e += blockDim.x) {
-        const int i = e / tbk, c = e % tbk;
-        A[(int64_t)(ro + i) * ld + o + c] = P[i][c];
-      }
-    }
-    grid_barrier(p.bar, G, gen);
-    if (k + 1 == nt) break;
-    // B. trailing updates of step k; CTA 0 takes tile (k+1, k+1) and factors it.
-    const int nrest = nt - k - 1;                      // trailing tile rows/cols: k+1 .. nt-1
-    const long long ntiles = (long long)nrest * (nrest + 1) / 2;
-    if (bid == 0) {
-      const int o1 = o + T, tb1 = tb_of(k + 1);
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        P[i][j] = (i < tb1 && j < tbk) ? A[(int64_t)(o1 + i) * ld + o + j] : 0.0;
-        S[i][j] = (i < tb1 && j <= i) ? A[(int64_t)(o1 + i) * ld + o1 + j] : 0.0;
-      }
-      __syncthreads();
-      // S -= P P^T (lower part), in shared memory
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        if (j <= i && i < tb1) {
-          double acc = 0.0;
-          for (int c = 0; c < tbk; ++c) acc = fma(P[i][c], P[j][c], acc);
-          S[i][j] -= acc;
-        }
-      }
-      __syncthreads();
-      coop_factor(S, rd, tb1, p.row0 + o1);
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        if (i < tb1 && j < tb1) A[(int64_t)(o1 + i) * ld + o1 + j] = S[i][j];
-      }
-      if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
-    }
-    // Tiles of the trailing lower triangle other than (k+1, k+1), spread over CTAs 1..G-1
-    // (CTA 0 joins when G == 1).
-    const int workers = G > 1 ? G - 1 : 1, wid = G > 1 ? bid - 1 : 0;
-    if (G == 1 || bid > 0) {
-      for (long long t = 1 + wid; t < ntiles; t += workers) {
-        int rr = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((long long)(rr + 1) * (rr + 2) / 2 <= t) ++rr;
-        while ((long long)rr * (rr + 1) / 2 > t) --rr;
-        const int cc = (int)(t - (long long)rr * (rr + 1) / 2);
-        const int r = k + 1 + rr, c = k + 1 + cc;
-        const int rb = tb_of(r), cb = tb_of(c);
-        __syncthreads();
-        for (int e = tid; e < T * T; e += blockDim.x) {
-          const int i = e / T, j = e % T;
-          P[i][j] = (i < rb && j < tbk) ? A[(int64_t)(r * T + i) * ld + o + j] : 0.0;
-          Q[i][j] = (i < cb && j < tbk) ? A[(int64_t)(c * T + i) * ld + o + j] : 0.0;
-        }
-        __syncthreads();
-        coop_tile_update(A + (int64_t)(r * T) * ld + c * T, ld, rb, cb, P, Q, T);
-      }
-    }
-    grid_barrier(p.bar, G, gen);
-  }
-  // Strict upper triangle of the block -> 0.
-  for (long long e = (long long)bid * blockDim.x + tid; e < (long long)p.nrow * p.nrow;
-       e += (long long)G * blockDim.x) {
-    const int i = (int)(e / p.nrow), j = (int)(e % p.nrow);
-    if (j > i) A[(int64_t)i * ld + j] = 0.0;
-  }
-}
-
-static int coop_grid(int nt) {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, potrf_coop_kernel, 256, 0);
-    cached = per >= 1 ? sms : 0;  // one CTA per SM: the FP64 pipe is per SM, barriers stay cheap
-  }
-  (void)nt;
-  return cached;
-}
-
-cudaError_t potrf_coop(double* A, int64_t ld, int nrow, long long info_row0, void* scratch,
-                       cudaStream_t s) {
-  CoopArgs p;
-  p.A = A;
-  p.ld = ld;
-  p.nrow = nrow;
-  p.row0 = info_row0;
-  p.bar = (CoopBar*)scratch;
-  p.rdiag = (double*)((char*)scratch + 256);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(CoopBar), s);
-  if (e != cudaSuccess) return e;
-  const int G = coop_grid((nrow + T - 1) / T);
-  if (G < 1) return cudaErrorInvalidConfiguration;
-  void* args[] = {&p};
-  TimedLaunch tl(K_POTRF_TILE, 0.0, s);
-  return cudaLaunchCooperativeKernel((void*)potrf_coop_kernel, dim3(G), dim3(256), args, 0, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -950,13 +795,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// Row of the lower-triangular index u (u = row (row + 1) / 2 + col, col <= row).
-__device__ __forceinline__ int tri_row(int u) {
-  int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-  while ((r + 1) * (r + 2) / 2 <= u) ++r;
-  while (r * (r + 1) / 2 > u) --r;
-  return r;
-}
 
 // Panel solve in shared memory: X (rows x tb) <- X L^{-T}, L lower in Lt, rdv = 1 / diag(L).
 __device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*Lt)[T + 1],
