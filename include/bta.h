@@ -61,8 +61,12 @@ typedef struct CUstream_st* bta_stream_t; /* same type as cudaStream_t */
  * block column and L_nn = POTRF(A_nn).
  * In: the lower triangles of diag[i] and tip (upper triangles are not read),
  * lower, arrow. Out: L in the same buffers; the strict upper triangles of diag[i]
- * and tip are set to zero. The triangular solves run as L_ii^{-1} followed by
- * products (the inverse-plus-GEMM substitution of Sections 4 and 5.1).
+ * and tip are set to zero. In FP64 (b >= 128) each block step is one cooperative
+ * launch: a tile Cholesky of the block column [A_ii; A_{i+1,i}; A_{n,i}] whose
+ * trailing tile updates are the step's Schur products; the triangular solves are
+ * tile substitutions. In the tensor-core precision modes the triangular solves
+ * run as L_ii^{-1} followed by products (the inverse-plus-GEMM substitution of
+ * Sections 4 and 5.1).
  * Errors: see the header comment; info = 1-based global row of the first
  * non-positive leading minor (block i, local row j -> i*b + j; tip -> n*b + j).
  */
@@ -89,7 +93,9 @@ int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
  * standard use of a Cholesky factor.
  *   y_i = L_ii^{-1}(r_i - L_{i,i-1} y_{i-1}),  y_n = L_nn^{-1}(r_n - sum_i L_{n,i} y_i)
  *   x_n = L_nn^{-T} y_n,  x_i = L_ii^{-T}(y_i - L_{i+1,i}^T x_{i+1} - L_{n,i}^T x_n)
- * rhs: [N][nrhs] row-major device buffer, 1 <= nrhs <= 64.
+ * rhs: [N][nrhs] row-major device buffer, 1 <= nrhs <= 64. Both sweeps use the
+ * inverses of the 32 x 32 diagonal tiles of every L_ii, formed first in the
+ * workspace (n * ceil(b/32) * 1024 doubles, besides the arrow partial sums).
  */
 int bta_solve(int64_t n, int64_t b, int64_t a, const double* diag,
               const double* lower, const double* arrow, const double* tip,
