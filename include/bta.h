@@ -280,11 +280,48 @@ int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const doub
 
 /*
  * bta_tc_status -- reads and clears the timeout flag of the library's bounded
- * waits (the tcgen05 pipelines' mbarriers and the cooperative POTRF's grid
- * barrier): 1 if any wait gave up since the last read (its results are then not
- * valid), else 0. Synchronous.
+ * waits (the tcgen05 pipelines' mbarriers, the cooperative factor step's grid
+ * barrier and flags): 1 if any wait gave up since the last read (its results are
+ * then not valid), else 0. Synchronous.
  */
 int bta_tc_status(int* timed_out);
+
+/*
+ * bta_factor_selinv_host -- the whole per-matrix sequence from host memory:
+ * factor (Algorithm 1), log det, a solve with nrhs right-hand sides (0: none)
+ * and the selected inversion (Algorithm 2), with the inputs copied in and X,
+ * the solution and log det copied back inside the call. The copies overlap the
+ * block sweeps: input blocks go up in chunks on a copy stream ahead of the
+ * factorization (step i waits only for blocks i and i+1), the solution as soon
+ * as the solve is done, and X chunk by chunk as the backward sweep finishes it.
+ * Layouts are those of bta_factor / bta_solve / bta_selinv; h_* inputs and x_*
+ * outputs are host buffers (pinned for the copies to overlap), h_logdet one host
+ * double. The host inputs are not modified. ws: device scratch of at least
+ * bta_host_pipeline_workspace_bytes(n, b, a, nrhs) bytes, 256-byte aligned; it
+ * holds the device copy of the pattern. Asynchronous on `stream` like the other
+ * entry points: outputs are valid once the stream has reached this point; the
+ * host buffers must stay valid until then. Calls must not overlap (they share
+ * the library's copy streams and events). Precision: bta_set_precision.
+ * Returns 0, -k for invalid argument k, or a CUDA error code; pivot failure goes
+ * to the info word as in bta_factor.
+ */
+size_t bta_host_pipeline_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t nrhs);
+int bta_factor_selinv_host(int64_t n, int64_t b, int64_t a, const double* h_diag,
+                           const double* h_lower, const double* h_arrow, const double* h_tip,
+                           const double* h_rhs, int64_t nrhs, double* x_diag, double* x_lower,
+                           double* x_arrow, double* x_tip, double* x_sol, double* h_logdet,
+                           void* ws, size_t ws_bytes, bta_stream_t stream);
+
+/*
+ * bta_wait_selftest -- exercises the timeout path of the library's bounded
+ * waits: one CTA waits, with a limit of `polls` polls (1 <= polls <= 2^20), on a
+ * device flag that nothing raises, gives up, records the timeout, and returns.
+ * *timed_out then receives bta_tc_status's reading (1 when the path works).
+ * Synchronous; allocates and frees 4 bytes of device memory. Not part of the
+ * method: it lets a test check failure reporting without faulting the GPU.
+ * Returns -1 for polls out of range, -2 for a null timed_out.
+ */
+int bta_wait_selftest(int64_t polls, int* timed_out);
 
 /* ---- Measurement support (not part of the method) ----------------------- */
 

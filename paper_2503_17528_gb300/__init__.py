@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     OP_SELINV,
     OP_SOLVE,
     factor,
+    factor_selinv_host,
     factor_selinv_partitioned,
     gemm,
     get_info,
@@ -27,6 +28,7 @@ from .api import (  # noqa: F401
     set_precision,
     solve,
     tc_status,
+    wait_selftest,
     workspace_bytes,
 )
 from .autograd import BTALogdetQuad, logdet_quad  # noqa: F401,E402

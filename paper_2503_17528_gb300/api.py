@@ -35,7 +35,7 @@ def _check(rc: int, name: str):
         raise BTAError(f"{name}: CUDA error {rc}")
 
 
-def _dims(diag, lower, arrow, tip):
+def _dims(diag, lower, arrow, tip, on_host=False):
     if diag.dim() != 3 or diag.shape[1] != diag.shape[2]:
         raise ValueError("diag must be [n, b, b]")
     n, b = diag.shape[0], diag.shape[1]
@@ -51,8 +51,9 @@ def _dims(diag, lower, arrow, tip):
     for t in (diag, lower, arrow, tip):
         if t is None:
             continue
-        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
-            raise ValueError("blocks must be contiguous float64 CUDA tensors")
+        if t.dtype != torch.float64 or t.is_cuda == on_host or not t.is_contiguous():
+            raise ValueError("blocks must be contiguous float64 " + ("CPU" if on_host else "CUDA")
+                             + " tensors")
         if t.device != diag.device:
             raise ValueError("all blocks must be on one device")
     return n, b, a
@@ -175,6 +176,47 @@ def tc_status() -> int:
     """1 if a tensor-core kernel gave up on a bounded wait since the last read."""
     v = ctypes.c_int(0)
     _check(_lib.load().bta_tc_status(ctypes.byref(v)), "bta_tc_status")
+    return int(v.value)
+
+
+def factor_selinv_host(diag, lower, arrow, tip, rhs=None, out=None, device=None):
+    """Factor, log det, solve (if rhs is given) and selected inversion of a matrix
+    held in host memory (CPU tensors; pinned ones let the copies overlap the
+    sweeps). Returns (x_diag, x_lower, x_arrow, x_tip, x, logdet) as CPU tensors
+    (`out`, if given, is that tuple preallocated); they are valid once the
+    current stream of `device` has finished (torch.cuda.synchronize)."""
+    n, b, a = _dims(diag, lower, arrow, tip, on_host=True)
+    for name, t in (("diag", diag), ("lower", lower), ("arrow", arrow), ("tip", tip), ("rhs", rhs)):
+        if t is not None and (t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 CPU tensor")
+    nrhs = 0 if rhs is None else (rhs.shape[1] if rhs.dim() == 2 else 1)
+    if rhs is not None and rhs.shape[0] != n * b + a:
+        raise ValueError("rhs must have n*b + a rows")
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out is None:
+        pin = diag.is_pinned()
+        def _e(t):
+            return None if t is None else torch.empty(t.shape, dtype=torch.float64, pin_memory=pin)
+        out = (_e(diag), _e(lower), _e(arrow), _e(tip), _e(rhs), torch.empty((), dtype=torch.float64,
+                                                                         pin_memory=pin))
+    lib = _lib.load()
+    with torch.cuda.device(device):
+        nbytes = int(lib.bta_host_pipeline_workspace_bytes(n, b, a, nrhs))
+        if nbytes == 0:
+            raise BTAError("bta_host_pipeline_workspace_bytes: invalid arguments")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        wp = ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+        _check(lib.bta_factor_selinv_host(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                          _ptr(rhs), nrhs, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                          _ptr(out[3]), _ptr(out[4]), _ptr(out[5]), wp, nbytes,
+                                          _stream(device)), "bta_factor_selinv_host")
+    return out
+
+
+def wait_selftest(polls: int = 1000) -> int:
+    """Runs the bounded-wait timeout self-test; 1 if the timeout was recorded."""
+    v = ctypes.c_int(0)
+    _check(_lib.load().bta_wait_selftest(int(polls), ctypes.byref(v)), "bta_wait_selftest")
     return int(v.value)
 
 

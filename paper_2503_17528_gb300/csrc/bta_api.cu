@@ -234,8 +234,13 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   return 0;
 }
 
+// Called after backward step i of the selected inversion, once diag[i],
+// lower[i] and arrow[i] hold their final X blocks (enqueue-time hook).
+typedef cudaError_t (*StepHook)(int64_t i, void* ctx);
+
 int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
-                double* tip, const SelinvWs& w, int prec, cudaStream_t s) {
+                double* tip, const SelinvWs& w, int prec, cudaStream_t s,
+                StepHook after = nullptr, void* after_ctx = nullptr) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b, ab = a * b;
   TcWs tw;
@@ -302,6 +307,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       g.t[g.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
     if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
     BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
+    if (after) BTA_TRY(after(i, after_ctx));
   }
   return 0;
 }
@@ -737,6 +743,178 @@ int partitioned_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lowe
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Host-buffer pipeline: factor + logdet + solve + selinv with the pattern
+// streamed in from host memory and X streamed back, the copies overlapped with
+// the block sweeps (inputs in chunks of blocks ahead of the factorization,
+// outputs as soon as the backward sweep has finished a chunk).
+// ---------------------------------------------------------------------------
+struct HostPipeWs {
+  double *diag, *lower, *arrow, *tip, *rhs, *ld;
+  FactorWs fw;
+  SelinvWs sw;
+  SolveWs vw;
+  LogdetWs lw;
+};
+
+size_t host_pipe_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, HostPipeWs* o, int prec) {
+  Carver c(p);
+  HostPipeWs w{};
+  w.diag = c.take((size_t)(n * b * b));
+  w.lower = c.take((size_t)((n - 1) * b * b + 1));
+  w.arrow = c.take((size_t)(n * a * b + 1));
+  w.tip = c.take((size_t)(a * a + 1));
+  w.rhs = c.take((size_t)((n * b + a) * (R > 0 ? R : 1)));
+  w.ld = c.take(1);
+  // factor, logdet, solve and selinv run one after another on one stream: their
+  // scratch shares one region.
+  char* sub = p ? (char*)p + c.off : nullptr;
+  size_t region = factor_ws(n, b, a, sub, &w.fw, prec);
+  region = std::max(region, selinv_ws(n, b, a, sub, &w.sw, prec));
+  if (R > 0) region = std::max(region, solve_ws(n, b, a, R, sub, &w.vw));
+  region = std::max(region, logdet_ws(n, sub, &w.lw));
+  c.off += align_up(region);
+  if (o) *o = w;
+  return c.off;
+}
+
+std::mutex g_ev_mu;
+std::vector<cudaEvent_t> g_events[64];
+
+cudaError_t events_for(size_t k, cudaEvent_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  std::vector<cudaEvent_t>& v = g_events[dev];
+  while (v.size() < k) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    v.push_back(ev);
+  }
+  *out = v.data();
+  return cudaSuccess;
+}
+
+struct HostPipe {
+  int64_t n, b, a, C;
+  const HostPipeWs* w;
+  double *xd, *xl, *xa;
+  cudaStream_t s, cout;
+  cudaEvent_t* evout;
+};
+
+// Blocks [i, i + C) are final: copy them back on the copy-out stream.
+cudaError_t pipe_after_step(int64_t i, void* ctx) {
+  HostPipe& h = *(HostPipe*)ctx;
+  if (i % h.C) return cudaSuccess;
+  const int64_t bb = h.b * h.b, ab = h.a * h.b, i1 = std::min(h.n, i + h.C);
+  cudaEvent_t ev = h.evout[i / h.C];
+  cudaError_t e = cudaEventRecord(ev, h.s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h.cout, ev, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(h.xd + i * bb, h.w->diag + i * bb, (i1 - i) * bb * sizeof(double),
+                      cudaMemcpyDeviceToHost, h.cout);
+  const int64_t l1 = std::min(h.n - 1, i1);
+  if (e == cudaSuccess && l1 > i)
+    e = cudaMemcpyAsync(h.xl + i * bb, h.w->lower + i * bb, (l1 - i) * bb * sizeof(double),
+                        cudaMemcpyDeviceToHost, h.cout);
+  if (e == cudaSuccess && h.a > 0)
+    e = cudaMemcpyAsync(h.xa + i * ab, h.w->arrow + i * ab, (i1 - i) * ab * sizeof(double),
+                        cudaMemcpyDeviceToHost, h.cout);
+  return e;
+}
+
+int host_pipe_impl(int64_t n, int64_t b, int64_t a, const double* hd, const double* hl,
+                   const double* ha, const double* ht, const double* hr, int64_t R, double* xd,
+                   double* xl, double* xa, double* xt, double* x, double* hld, const HostPipeWs& w,
+                   int prec, cudaStream_t s) {
+  const int64_t bb = b * b, ab = a * b;
+  // Chunks of about 32 MB of input (at least one block).
+  const int64_t per_block = (2 * bb + ab) * (int64_t)sizeof(double);
+  const int64_t C = std::max<int64_t>(1, std::min<int64_t>(n, (32ll << 20) / per_block));
+  const int64_t nch = (n + C - 1) / C;
+  StreamPool* pool = nullptr;
+  BTA_TRY(pool_for(2, &pool));
+  cudaStream_t cin = pool->streams[0], cout = pool->streams[1];
+  cudaEvent_t* ev = nullptr;
+  BTA_TRY(events_for((size_t)(2 * nch + 3), &ev));
+  cudaEvent_t ev_start = ev[0], ev_solved = ev[1], ev_done = ev[2];
+  cudaEvent_t* evin = ev + 3;
+  cudaEvent_t* evout = ev + 3 + nch;
+  // The copy streams start after the caller's earlier work on s.
+  BTA_TRY(cudaEventRecord(ev_start, s));
+  BTA_TRY(cudaStreamWaitEvent(cin, ev_start, 0));
+  BTA_TRY(cudaStreamWaitEvent(cout, ev_start, 0));
+  // Inputs: tip and right-hand sides first, then the blocks chunk by chunk.
+  if (a > 0)
+    BTA_TRY(cudaMemcpyAsync(w.tip, ht, a * a * sizeof(double), cudaMemcpyHostToDevice, cin));
+  if (R > 0)
+    BTA_TRY(cudaMemcpyAsync(w.rhs, hr, (n * b + a) * R * sizeof(double), cudaMemcpyHostToDevice,
+                            cin));
+  for (int64_t c = 0; c < nch; ++c) {
+    const int64_t i0 = c * C, i1 = std::min(n, i0 + C), l1 = std::min(n - 1, i1);
+    BTA_TRY(cudaMemcpyAsync(w.diag + i0 * bb, hd + i0 * bb, (i1 - i0) * bb * sizeof(double),
+                            cudaMemcpyHostToDevice, cin));
+    if (l1 > i0)
+      BTA_TRY(cudaMemcpyAsync(w.lower + i0 * bb, hl + i0 * bb, (l1 - i0) * bb * sizeof(double),
+                              cudaMemcpyHostToDevice, cin));
+    if (a > 0)
+      BTA_TRY(cudaMemcpyAsync(w.arrow + i0 * ab, ha + i0 * ab, (i1 - i0) * ab * sizeof(double),
+                              cudaMemcpyHostToDevice, cin));
+    BTA_TRY(cudaEventRecord(evin[c], cin));
+  }
+  // Factor: step i needs blocks i and i+1 on the device.
+  int64_t waited = -1;
+  auto wait_block = [&](int64_t i) -> cudaError_t {
+    const int64_t c = std::min(i, n - 1) / C;
+    while (waited < c) {
+      ++waited;
+      cudaError_t e = cudaStreamWaitEvent(s, evin[waited], 0);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (b >= kCoopMinB && prec == BTA_PREC_FP64) {
+    for (int64_t i = 0; i < n; ++i) {
+      const bool nx = i + 1 < n;
+      BTA_TRY(wait_block(i + 1));
+      BTA_TRY(factor_step_coop(w.diag + i * bb, nx ? w.lower + i * bb : nullptr,
+                               nx ? w.diag + (i + 1) * bb : nullptr, a > 0 ? w.arrow + i * ab : nullptr,
+                               (a > 0 && nx) ? w.arrow + (i + 1) * ab : nullptr, a > 0 ? w.tip : nullptr,
+                               (int)b, (int)a, nx ? 1 : 0, i * b, w.fw.coop, s));
+    }
+    if (a > 0) BTA_TRY(potrf_blocks(w.tip, a, a * a, 1, (int)a, n * b, 0, s));
+  } else {
+    BTA_TRY(wait_block(n - 1));
+    const int rc = factor_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.fw, prec, s);
+    if (rc) return rc;
+  }
+  BTA_TRY(logdet_f64(w.diag, n, b, w.tip, a, w.lw.partial, w.ld, s));
+  BTA_TRY(cudaMemcpyAsync(hld, w.ld, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (R > 0) {
+    const int rc = solve_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.rhs, R, w.vw, s);
+    if (rc) return rc;
+    BTA_TRY(cudaEventRecord(ev_solved, s));
+    BTA_TRY(cudaStreamWaitEvent(cout, ev_solved, 0));
+    BTA_TRY(cudaMemcpyAsync(x, w.rhs, (n * b + a) * R * sizeof(double), cudaMemcpyDeviceToHost,
+                            cout));
+  }
+  HostPipe hp{n, b, a, C, &w, xd, xl, xa, s, cout, evout};
+  {
+    const int rc = selinv_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.sw, prec, s,
+                               pipe_after_step, &hp);
+    if (rc) return rc;
+  }
+  if (a > 0)  // X_nn is final since the prologue; chunk 0's event follows it
+    BTA_TRY(cudaMemcpyAsync(xt, w.tip, a * a * sizeof(double), cudaMemcpyDeviceToHost, cout));
+  BTA_TRY(cudaEventRecord(ev_done, cout));
+  BTA_TRY(cudaStreamWaitEvent(s, ev_done, 0));
+  return 0;
+}
+
 extern "C" {
 
 int bta_version(void) { return 100; }
@@ -942,6 +1120,39 @@ int bta_factor_selinv_partitioned(int64_t n, int64_t b, int64_t a, double* diag,
   return partitioned_impl(n, b, a, diag, lower, arrow, tip, logdet_out, L, prec, (cudaStream_t)stream);
 }
 
+size_t bta_host_pipeline_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t nrhs) {
+  if (check_sizes(n, b, a) || nrhs < 0 || nrhs > 64) return 0;
+  return host_pipe_ws(n, b, a, nrhs, nullptr, nullptr, g_prec);
+}
+
+int bta_factor_selinv_host(int64_t n, int64_t b, int64_t a, const double* h_diag,
+                           const double* h_lower, const double* h_arrow, const double* h_tip,
+                           const double* h_rhs, int64_t nrhs, double* x_diag, double* x_lower,
+                           double* x_arrow, double* x_tip, double* x_sol, double* h_logdet,
+                           void* ws, size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (rc) return rc;
+  if (!h_diag || misaligned(h_diag)) return -4;
+  if (n > 1 && (!h_lower || misaligned(h_lower))) return -5;
+  if (a > 0 && (!h_arrow || misaligned(h_arrow))) return -6;
+  if (a > 0 && (!h_tip || misaligned(h_tip))) return -7;
+  if (nrhs < 0 || nrhs > 64) return -9;
+  if (nrhs > 0 && (!h_rhs || misaligned(h_rhs))) return -8;
+  if (!x_diag || misaligned(x_diag)) return -10;
+  if (n > 1 && (!x_lower || misaligned(x_lower))) return -11;
+  if (a > 0 && (!x_arrow || misaligned(x_arrow))) return -12;
+  if (a > 0 && (!x_tip || misaligned(x_tip))) return -13;
+  if (nrhs > 0 && (!x_sol || misaligned(x_sol))) return -14;
+  if (!h_logdet || misaligned(h_logdet)) return -15;
+  HostPipeWs w;
+  const int prec = g_prec;
+  const size_t need = host_pipe_ws(n, b, a, nrhs, ws, &w, prec);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -16;
+  if (ws_bytes < need) return -17;
+  return host_pipe_impl(n, b, a, h_diag, h_lower, h_arrow, h_tip, h_rhs, nrhs, x_diag, x_lower,
+                        x_arrow, x_tip, x_sol, h_logdet, w, prec, (cudaStream_t)stream);
+}
+
 int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,
                         bta_stream_t stream) {
   if (!out_dev) return -1;
@@ -1025,6 +1236,19 @@ int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const doub
   if (ws_bytes < tc_workspace_bytes(mode, (int)M, (int)N, (int)K, 1)) return -16;
   BTA_TRY(gemm_tc(g, mode, ws, ws_bytes, (cudaStream_t)stream));
   return 0;
+}
+
+int bta_wait_selftest(int64_t polls, int* timed_out) {
+  if (!timed_out) return -2;
+  if (polls < 1 || polls > (1 << 20)) return -1;
+  int* flag = nullptr;
+  BTA_TRY(cudaMalloc(&flag, sizeof(int)));
+  cudaError_t e = cudaMemset(flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = wait_selftest(flag, (unsigned)polls, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(flag);
+  if (e != cudaSuccess) return (int)e;
+  return bta_tc_status(timed_out);
 }
 
 int bta_tc_status(int* timed_out) {

@@ -75,6 +75,8 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
                              void* scratch, cudaStream_t s);
 // Reads and clears the timeout flag of the cooperative kernels' grid barriers.
 cudaError_t wait_error_read_reset(int* out);
+// Enqueues one CTA that waits on *flag_dev (never raised) for `polls` polls.
+cudaError_t wait_selftest(const int* flag_dev, unsigned polls, cudaStream_t s);
 
 // Inverse of lower-triangular blocks: Linv (separate buffer, same layout) =
 // L^{-1}, strict upper triangle zero. The doubling products go through `hook`

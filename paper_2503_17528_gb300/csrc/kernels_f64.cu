@@ -813,12 +813,13 @@ __device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*L
 }
 
 // Bounded wait until *flag >= v (a flag another CTA of the same cooperative
-// launch raises); on timeout the error word is set and the CTA goes on.
-__device__ __forceinline__ void wait_flag_ge(const int* flag, int v) {
+// launch raises); after max_polls polls the error word is set and the CTA goes on.
+__device__ __forceinline__ void wait_flag_ge(const int* flag, int v,
+                                             unsigned max_polls = 1u << 24) {
   if (threadIdx.x == 0) {
     unsigned polls = 0;
     while (atomicAdd((int*)flag, 0) < v) {
-      if (++polls > (1u << 24)) {
+      if (++polls > max_polls) {
         atomicExch(&g_wait_error, 1);
         break;
       }
@@ -1121,6 +1122,17 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
                                      0, s);
 }
 
+// Self-test of the bounded wait: one CTA waits on a flag that nothing raises,
+// with a poll limit of `polls`, so the wait gives up and records the timeout.
+__global__ void wait_selftest_kernel(const int* flag, unsigned polls) {
+  wait_flag_ge(flag, 1, polls);
+}
+
+cudaError_t wait_selftest(const int* flag_dev, unsigned polls, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 64, 0, s>>>(flag_dev, polls);
+  return cudaGetLastError();
+}
+
 cudaError_t wait_error_read_reset(int* out) {
   int v = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&v, g_wait_error, sizeof(int));
@@ -1332,7 +1344,7 @@ __device__ __forceinline__ double trsv_tile_el(const double* L, int64_t ld, int 
   return trans ? L[(int64_t)(o + c) * ld + ro + i] : L[(int64_t)(ro + i) * ld + o + c];
 }
 
-__global__ void __launch_bounds__(256) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
+__global__ void __launch_bounds__(256, 1) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
                                                            const double* Dinv, double* x,
                                                            int64_t ldx, int R, int trans) {
   __shared__ double Xk[T][65];

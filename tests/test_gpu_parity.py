@@ -21,6 +21,7 @@ SHAPES = [
     (7, 100, 33), (3, 96, 40), (9, 17, 2), (6, 128, 8), (2, 1, 1), (4, 1, 0),
     (3, 200, 5), (2, 300, 0), (4, 160, 17),  # one fused launch per block step, ragged last tile
     (1, 128, 0), (1, 150, 9), (2, 130, 40), (3, 256, 70),  # one block; arrow rows over 2-3 tiles
+    (2, 520, 3),  # 17 row tiles: 16-CTA solve clusters, two tiles on one CTA, ragged last tile
 ]
 
 
