@@ -287,6 +287,24 @@ int bta_gemm(int prec, int64_t M, int64_t N, int64_t K, double alpha, const doub
 int bta_tc_status(int* timed_out);
 
 /*
+ * bta_factor_selinv_all -- the per-matrix sequence on device buffers in one
+ * call: bta_factor, bta_logdet (into logdet_out, one device double), bta_solve
+ * of rhs (nrhs right-hand sides, 0: none; in place) and bta_selinv (A -> X in
+ * place), with the same results as those four calls in a row. The solve runs on
+ * a library stream concurrently with the part of the selected inversion's
+ * prologue that only reads the factor (L_ii^{-1}, G_i, H_i); the selected
+ * inversion waits for it before writing into the factor's blocks. ws: device
+ * scratch of at least bta_all_workspace_bytes(n, b, a, nrhs) bytes, 256-byte
+ * aligned. Asynchronous on `stream`; calls must not overlap (they share the
+ * library's side streams and events). Returns 0, -k for invalid argument k, or a
+ * CUDA error code; pivot failure goes to the info word as in bta_factor.
+ */
+size_t bta_all_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t nrhs);
+int bta_factor_selinv_all(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                          double* arrow, double* tip, double* rhs, int64_t nrhs, double* logdet_out,
+                          void* ws, size_t ws_bytes, bta_stream_t stream);
+
+/*
  * bta_factor_selinv_host -- the whole per-matrix sequence from host memory:
  * factor (Algorithm 1), log det, a solve with nrhs right-hand sides (0: none)
  * and the selected inversion (Algorithm 2), with the inputs copied in and X,

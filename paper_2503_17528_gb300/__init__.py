@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     OP_SELINV,
     OP_SOLVE,
     factor,
+    factor_selinv_all,
     factor_selinv_host,
     factor_selinv_partitioned,
     gemm,

@@ -48,6 +48,8 @@ _SIGS = {
     "bta_tc_status": [ctypes.POINTER(ctypes.c_int)],
     "bta_wait_selftest": [_i64, ctypes.POINTER(ctypes.c_int)],
     "bta_host_pipeline_workspace_bytes": [_i64, _i64, _i64, _i64],
+    "bta_all_workspace_bytes": [_i64, _i64, _i64, _i64],
+    "bta_factor_selinv_all": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _p, _sz, _p],
     "bta_factor_selinv_host": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p, _p, _p,
                                _p, _sz, _p],
     "bta_version": [],

@@ -179,6 +179,33 @@ def tc_status() -> int:
     return int(v.value)
 
 
+def factor_selinv_all(diag, lower, arrow, tip, rhs=None, logdet_out=None):
+    """factor + logdet + solve (if rhs is given, in place) + selinv (A -> X in
+    place) in one call, the solve overlapped with the selected inversion's
+    prologue. Returns log det A as a 0-d CUDA tensor."""
+    n, b, a = _dims(diag, lower, arrow, tip)
+    nrhs = 0
+    if rhs is not None:
+        if rhs.dtype != torch.float64 or not rhs.is_cuda or not rhs.is_contiguous():
+            raise ValueError("rhs must be a contiguous float64 CUDA tensor")
+        if rhs.shape[0] != n * b + a:
+            raise ValueError("rhs must have n*b + a rows")
+        nrhs = rhs.shape[1] if rhs.dim() == 2 else 1
+    if logdet_out is None:
+        logdet_out = torch.empty((), dtype=torch.float64, device=diag.device)
+    lib = _lib.load()
+    with torch.cuda.device(diag.device):
+        nbytes = int(lib.bta_all_workspace_bytes(n, b, a, nrhs))
+        if nbytes == 0:
+            raise BTAError("bta_all_workspace_bytes: invalid arguments")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=diag.device)
+        wp = ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+        _check(lib.bta_factor_selinv_all(n, b, a, _ptr(diag), _ptr(lower), _ptr(arrow), _ptr(tip),
+                                         _ptr(rhs), nrhs, _ptr(logdet_out), wp, nbytes,
+                                         _stream(diag.device)), "bta_factor_selinv_all")
+    return logdet_out
+
+
 def factor_selinv_host(diag, lower, arrow, tip, rhs=None, out=None, device=None):
     """Factor, log det, solve (if rhs is given) and selected inversion of a matrix
     held in host memory (CPU tensors; pinned ones let the copies overlap the

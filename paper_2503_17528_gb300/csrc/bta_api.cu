@@ -238,9 +238,13 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
 // lower[i] and arrow[i] hold their final X blocks (enqueue-time hook).
 typedef cudaError_t (*StepHook)(int64_t i, void* ctx);
 
+// before_write (called with i = -1) runs once the prologue has formed every
+// product that only reads L (L_ii^{-1}, G_i, H_i), before the first write into
+// the factor's blocks (M_i into diag, X_nn into the tip).
 int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
                 double* tip, const SelinvWs& w, int prec, cudaStream_t s,
-                StepHook after = nullptr, void* after_ctx = nullptr) {
+                StepHook after = nullptr, void* after_ctx = nullptr,
+                StepHook before_write = nullptr, void* bw_ctx = nullptr) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b, ab = a * b;
   TcWs tw;
@@ -261,6 +265,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     g.t[0].sA1 = ab; g.t[0].sB1 = bb; g.sC1 = ab; g.nb1 = (int)n;
     BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
+  if (before_write) BTA_TRY(before_write(-1, bw_ctx));
   {
     GemmArgs g = one_term(term(w.Linv, b, OP_T, TRI_UPPER, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           diag, b, B, B, 0.0, 1);
@@ -744,36 +749,44 @@ int partitioned_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lowe
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Host-buffer pipeline: factor + logdet + solve + selinv with the pattern
-// streamed in from host memory and X streamed back, the copies overlapped with
-// the block sweeps (inputs in chunks of blocks ahead of the factorization,
-// outputs as soon as the backward sweep has finished a chunk).
+// The whole per-matrix sequence in one call: factor, log det, solve, selinv.
+// The solve only reads the factor, and so does the part of the selected
+// inversion's prologue that forms L_ii^{-1}, G_i and H_i: the solve runs on a
+// side stream concurrently with them, and the selected inversion waits for it
+// before its first write into the factor's blocks. From host memory (host mode)
+// the pattern is also streamed in by chunks of blocks ahead of the factor sweep
+// and X streamed back behind the backward sweep.
 // ---------------------------------------------------------------------------
-struct HostPipeWs {
-  double *diag, *lower, *arrow, *tip, *rhs, *ld;
+struct PipeWs {
+  double *diag, *lower, *arrow, *tip, *rhs, *ld;  // device copies (host mode)
   FactorWs fw;
   SelinvWs sw;
   SolveWs vw;
   LogdetWs lw;
 };
 
-size_t host_pipe_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, HostPipeWs* o, int prec) {
+size_t pipe_ws(int64_t n, int64_t b, int64_t a, int64_t R, bool host, void* p, PipeWs* o, int prec) {
   Carver c(p);
-  HostPipeWs w{};
-  w.diag = c.take((size_t)(n * b * b));
-  w.lower = c.take((size_t)((n - 1) * b * b + 1));
-  w.arrow = c.take((size_t)(n * a * b + 1));
-  w.tip = c.take((size_t)(a * a + 1));
-  w.rhs = c.take((size_t)((n * b + a) * (R > 0 ? R : 1)));
-  w.ld = c.take(1);
-  // factor, logdet, solve and selinv run one after another on one stream: their
-  // scratch shares one region.
+  PipeWs w{};
+  if (host) {
+    w.diag = c.take((size_t)(n * b * b));
+    w.lower = c.take((size_t)((n - 1) * b * b + 1));
+    w.arrow = c.take((size_t)(n * a * b + 1));
+    w.tip = c.take((size_t)(a * a + 1));
+    w.rhs = c.take((size_t)((n * b + a) * (R > 0 ? R : 1)));
+    w.ld = c.take(1);
+  }
+  // factor, log det and selinv run one after another on the caller's stream and
+  // share one scratch region; the solve, concurrent with selinv, has its own.
   char* sub = p ? (char*)p + c.off : nullptr;
   size_t region = factor_ws(n, b, a, sub, &w.fw, prec);
   region = std::max(region, selinv_ws(n, b, a, sub, &w.sw, prec));
-  if (R > 0) region = std::max(region, solve_ws(n, b, a, R, sub, &w.vw));
   region = std::max(region, logdet_ws(n, sub, &w.lw));
   c.off += align_up(region);
+  if (R > 0) {
+    const size_t vsz = solve_ws(n, b, a, R, p ? (char*)p + c.off : nullptr, &w.vw);
+    c.off += align_up(vsz);
+  }
   if (o) *o = w;
   return c.off;
 }
@@ -798,77 +811,102 @@ cudaError_t events_for(size_t k, cudaEvent_t** out) {
   return cudaSuccess;
 }
 
-struct HostPipe {
+struct PipeCtx {
   int64_t n, b, a, C;
-  const HostPipeWs* w;
-  double *xd, *xl, *xa;
+  double *diag, *lower, *arrow;  // device blocks
+  double *xd, *xl, *xa;          // host outputs (host mode)
   cudaStream_t s, cout;
   cudaEvent_t* evout;
+  cudaEvent_t ev_solved;
+  bool host, solving;
 };
 
 // Blocks [i, i + C) are final: copy them back on the copy-out stream.
 cudaError_t pipe_after_step(int64_t i, void* ctx) {
-  HostPipe& h = *(HostPipe*)ctx;
-  if (i % h.C) return cudaSuccess;
+  PipeCtx& h = *(PipeCtx*)ctx;
+  if (!h.host || i % h.C) return cudaSuccess;
   const int64_t bb = h.b * h.b, ab = h.a * h.b, i1 = std::min(h.n, i + h.C);
   cudaEvent_t ev = h.evout[i / h.C];
   cudaError_t e = cudaEventRecord(ev, h.s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h.cout, ev, 0);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(h.xd + i * bb, h.w->diag + i * bb, (i1 - i) * bb * sizeof(double),
+  e = cudaMemcpyAsync(h.xd + i * bb, h.diag + i * bb, (i1 - i) * bb * sizeof(double),
                       cudaMemcpyDeviceToHost, h.cout);
   const int64_t l1 = std::min(h.n - 1, i1);
   if (e == cudaSuccess && l1 > i)
-    e = cudaMemcpyAsync(h.xl + i * bb, h.w->lower + i * bb, (l1 - i) * bb * sizeof(double),
+    e = cudaMemcpyAsync(h.xl + i * bb, h.lower + i * bb, (l1 - i) * bb * sizeof(double),
                         cudaMemcpyDeviceToHost, h.cout);
   if (e == cudaSuccess && h.a > 0)
-    e = cudaMemcpyAsync(h.xa + i * ab, h.w->arrow + i * ab, (i1 - i) * ab * sizeof(double),
+    e = cudaMemcpyAsync(h.xa + i * ab, h.arrow + i * ab, (i1 - i) * ab * sizeof(double),
                         cudaMemcpyDeviceToHost, h.cout);
   return e;
 }
 
-int host_pipe_impl(int64_t n, int64_t b, int64_t a, const double* hd, const double* hl,
-                   const double* ha, const double* ht, const double* hr, int64_t R, double* xd,
-                   double* xl, double* xa, double* xt, double* x, double* hld, const HostPipeWs& w,
-                   int prec, cudaStream_t s) {
+// The selected inversion's first write into the factor: the solve must be done.
+cudaError_t pipe_before_write(int64_t, void* ctx) {
+  PipeCtx& h = *(PipeCtx*)ctx;
+  return h.solving ? cudaStreamWaitEvent(h.s, h.ev_solved, 0) : cudaSuccess;
+}
+
+// Host mode: h* are host inputs, x* host outputs, the blocks live in w's device
+// copies. Device mode: d* are the caller's device blocks (in place) and rhs its
+// device right-hand sides; ld_dev receives log det.
+struct PipeArgs {
+  bool host;
+  const double *hd, *hl, *ha, *ht, *hr;  // host inputs
+  double *xd, *xl, *xa, *xt, *x, *hld;   // host outputs
+  double *dd, *dl, *da, *dt, *dr, *ld_dev;  // device blocks (device mode)
+};
+
+int pipeline_impl(int64_t n, int64_t b, int64_t a, int64_t R, const PipeArgs& io, const PipeWs& w,
+                  int prec, cudaStream_t s) {
   const int64_t bb = b * b, ab = a * b;
+  double* diag = io.host ? w.diag : io.dd;
+  double* lower = io.host ? w.lower : io.dl;
+  double* arrow = io.host ? w.arrow : io.da;
+  double* tip = io.host ? w.tip : io.dt;
+  double* rhs = io.host ? w.rhs : io.dr;
+  double* ld = io.host ? w.ld : io.ld_dev;
   // Chunks of about 32 MB of input (at least one block).
   const int64_t per_block = (2 * bb + ab) * (int64_t)sizeof(double);
   const int64_t C = std::max<int64_t>(1, std::min<int64_t>(n, (32ll << 20) / per_block));
-  const int64_t nch = (n + C - 1) / C;
+  const int64_t nch = io.host ? (n + C - 1) / C : 0;
   StreamPool* pool = nullptr;
-  BTA_TRY(pool_for(2, &pool));
-  cudaStream_t cin = pool->streams[0], cout = pool->streams[1];
+  BTA_TRY(pool_for(3, &pool));
+  cudaStream_t cin = pool->streams[0], cout = pool->streams[1], cs = pool->streams[2];
   cudaEvent_t* ev = nullptr;
-  BTA_TRY(events_for((size_t)(2 * nch + 3), &ev));
-  cudaEvent_t ev_start = ev[0], ev_solved = ev[1], ev_done = ev[2];
-  cudaEvent_t* evin = ev + 3;
-  cudaEvent_t* evout = ev + 3 + nch;
-  // The copy streams start after the caller's earlier work on s.
-  BTA_TRY(cudaEventRecord(ev_start, s));
-  BTA_TRY(cudaStreamWaitEvent(cin, ev_start, 0));
-  BTA_TRY(cudaStreamWaitEvent(cout, ev_start, 0));
-  // Inputs: tip and right-hand sides first, then the blocks chunk by chunk.
-  if (a > 0)
-    BTA_TRY(cudaMemcpyAsync(w.tip, ht, a * a * sizeof(double), cudaMemcpyHostToDevice, cin));
-  if (R > 0)
-    BTA_TRY(cudaMemcpyAsync(w.rhs, hr, (n * b + a) * R * sizeof(double), cudaMemcpyHostToDevice,
-                            cin));
-  for (int64_t c = 0; c < nch; ++c) {
-    const int64_t i0 = c * C, i1 = std::min(n, i0 + C), l1 = std::min(n - 1, i1);
-    BTA_TRY(cudaMemcpyAsync(w.diag + i0 * bb, hd + i0 * bb, (i1 - i0) * bb * sizeof(double),
-                            cudaMemcpyHostToDevice, cin));
-    if (l1 > i0)
-      BTA_TRY(cudaMemcpyAsync(w.lower + i0 * bb, hl + i0 * bb, (l1 - i0) * bb * sizeof(double),
-                              cudaMemcpyHostToDevice, cin));
+  BTA_TRY(events_for((size_t)(2 * nch + 4), &ev));
+  cudaEvent_t ev_start = ev[0], ev_factored = ev[1], ev_solved = ev[2], ev_done = ev[3];
+  cudaEvent_t* evin = ev + 4;
+  cudaEvent_t* evout = ev + 4 + nch;
+  if (io.host) {
+    // The copy streams start after the caller's earlier work on s. Inputs: tip
+    // and right-hand sides first, then the blocks chunk by chunk.
+    BTA_TRY(cudaEventRecord(ev_start, s));
+    BTA_TRY(cudaStreamWaitEvent(cin, ev_start, 0));
+    BTA_TRY(cudaStreamWaitEvent(cout, ev_start, 0));
     if (a > 0)
-      BTA_TRY(cudaMemcpyAsync(w.arrow + i0 * ab, ha + i0 * ab, (i1 - i0) * ab * sizeof(double),
+      BTA_TRY(cudaMemcpyAsync(tip, io.ht, a * a * sizeof(double), cudaMemcpyHostToDevice, cin));
+    if (R > 0)
+      BTA_TRY(cudaMemcpyAsync(rhs, io.hr, (n * b + a) * R * sizeof(double), cudaMemcpyHostToDevice,
+                              cin));
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t i0 = c * C, i1 = std::min(n, i0 + C), l1 = std::min(n - 1, i1);
+      BTA_TRY(cudaMemcpyAsync(diag + i0 * bb, io.hd + i0 * bb, (i1 - i0) * bb * sizeof(double),
                               cudaMemcpyHostToDevice, cin));
-    BTA_TRY(cudaEventRecord(evin[c], cin));
+      if (l1 > i0)
+        BTA_TRY(cudaMemcpyAsync(lower + i0 * bb, io.hl + i0 * bb, (l1 - i0) * bb * sizeof(double),
+                                cudaMemcpyHostToDevice, cin));
+      if (a > 0)
+        BTA_TRY(cudaMemcpyAsync(arrow + i0 * ab, io.ha + i0 * ab, (i1 - i0) * ab * sizeof(double),
+                                cudaMemcpyHostToDevice, cin));
+      BTA_TRY(cudaEventRecord(evin[c], cin));
+    }
   }
   // Factor: step i needs blocks i and i+1 on the device.
   int64_t waited = -1;
   auto wait_block = [&](int64_t i) -> cudaError_t {
+    if (!io.host) return cudaSuccess;
     const int64_t c = std::min(i, n - 1) / C;
     while (waited < c) {
       ++waited;
@@ -881,37 +919,45 @@ int host_pipe_impl(int64_t n, int64_t b, int64_t a, const double* hd, const doub
     for (int64_t i = 0; i < n; ++i) {
       const bool nx = i + 1 < n;
       BTA_TRY(wait_block(i + 1));
-      BTA_TRY(factor_step_coop(w.diag + i * bb, nx ? w.lower + i * bb : nullptr,
-                               nx ? w.diag + (i + 1) * bb : nullptr, a > 0 ? w.arrow + i * ab : nullptr,
-                               (a > 0 && nx) ? w.arrow + (i + 1) * ab : nullptr, a > 0 ? w.tip : nullptr,
+      BTA_TRY(factor_step_coop(diag + i * bb, nx ? lower + i * bb : nullptr,
+                               nx ? diag + (i + 1) * bb : nullptr, a > 0 ? arrow + i * ab : nullptr,
+                               (a > 0 && nx) ? arrow + (i + 1) * ab : nullptr, a > 0 ? tip : nullptr,
                                (int)b, (int)a, nx ? 1 : 0, i * b, w.fw.coop, s));
     }
-    if (a > 0) BTA_TRY(potrf_blocks(w.tip, a, a * a, 1, (int)a, n * b, 0, s));
+    if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, (int)a, n * b, 0, s));
   } else {
     BTA_TRY(wait_block(n - 1));
-    const int rc = factor_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.fw, prec, s);
+    const int rc = factor_impl(n, b, a, diag, lower, arrow, tip, w.fw, prec, s);
     if (rc) return rc;
   }
-  BTA_TRY(logdet_f64(w.diag, n, b, w.tip, a, w.lw.partial, w.ld, s));
-  BTA_TRY(cudaMemcpyAsync(hld, w.ld, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BTA_TRY(logdet_f64(diag, n, b, tip, a, w.lw.partial, ld, s));
+  if (io.host) BTA_TRY(cudaMemcpyAsync(io.hld, ld, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (R > 0) {
-    const int rc = solve_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.rhs, R, w.vw, s);
+    // The solve on the side stream, concurrent with the selinv prologue.
+    BTA_TRY(cudaEventRecord(ev_factored, s));
+    BTA_TRY(cudaStreamWaitEvent(cs, ev_factored, 0));
+    const int rc = solve_impl(n, b, a, diag, lower, arrow, tip, rhs, R, w.vw, cs);
     if (rc) return rc;
-    BTA_TRY(cudaEventRecord(ev_solved, s));
-    BTA_TRY(cudaStreamWaitEvent(cout, ev_solved, 0));
-    BTA_TRY(cudaMemcpyAsync(x, w.rhs, (n * b + a) * R * sizeof(double), cudaMemcpyDeviceToHost,
-                            cout));
+    BTA_TRY(cudaEventRecord(ev_solved, cs));
+    if (io.host) {
+      BTA_TRY(cudaStreamWaitEvent(cout, ev_solved, 0));
+      BTA_TRY(cudaMemcpyAsync(io.x, rhs, (n * b + a) * R * sizeof(double), cudaMemcpyDeviceToHost,
+                              cout));
+    }
   }
-  HostPipe hp{n, b, a, C, &w, xd, xl, xa, s, cout, evout};
+  PipeCtx hp{n, b, a, C, diag, lower, arrow, io.xd, io.xl, io.xa, s, cout, evout, ev_solved,
+             io.host, R > 0};
   {
-    const int rc = selinv_impl(n, b, a, w.diag, w.lower, w.arrow, w.tip, w.sw, prec, s,
-                               pipe_after_step, &hp);
+    const int rc = selinv_impl(n, b, a, diag, lower, arrow, tip, w.sw, prec, s, pipe_after_step, &hp,
+                               pipe_before_write, &hp);
     if (rc) return rc;
   }
-  if (a > 0)  // X_nn is final since the prologue; chunk 0's event follows it
-    BTA_TRY(cudaMemcpyAsync(xt, w.tip, a * a * sizeof(double), cudaMemcpyDeviceToHost, cout));
-  BTA_TRY(cudaEventRecord(ev_done, cout));
-  BTA_TRY(cudaStreamWaitEvent(s, ev_done, 0));
+  if (io.host) {
+    if (a > 0)  // X_nn is final since the prologue; it follows chunk 0's event
+      BTA_TRY(cudaMemcpyAsync(io.xt, tip, a * a * sizeof(double), cudaMemcpyDeviceToHost, cout));
+    BTA_TRY(cudaEventRecord(ev_done, cout));
+    BTA_TRY(cudaStreamWaitEvent(s, ev_done, 0));
+  }
   return 0;
 }
 
@@ -1122,7 +1168,7 @@ int bta_factor_selinv_partitioned(int64_t n, int64_t b, int64_t a, double* diag,
 
 size_t bta_host_pipeline_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t nrhs) {
   if (check_sizes(n, b, a) || nrhs < 0 || nrhs > 64) return 0;
-  return host_pipe_ws(n, b, a, nrhs, nullptr, nullptr, g_prec);
+  return pipe_ws(n, b, a, nrhs, true, nullptr, nullptr, g_prec);
 }
 
 int bta_factor_selinv_host(int64_t n, int64_t b, int64_t a, const double* h_diag,
@@ -1144,13 +1190,41 @@ int bta_factor_selinv_host(int64_t n, int64_t b, int64_t a, const double* h_diag
   if (a > 0 && (!x_tip || misaligned(x_tip))) return -13;
   if (nrhs > 0 && (!x_sol || misaligned(x_sol))) return -14;
   if (!h_logdet || misaligned(h_logdet)) return -15;
-  HostPipeWs w;
+  PipeWs w;
   const int prec = g_prec;
-  const size_t need = host_pipe_ws(n, b, a, nrhs, ws, &w, prec);
+  const size_t need = pipe_ws(n, b, a, nrhs, true, ws, &w, prec);
   if (!ws || ((uintptr_t)ws % kAlign)) return -16;
   if (ws_bytes < need) return -17;
-  return host_pipe_impl(n, b, a, h_diag, h_lower, h_arrow, h_tip, h_rhs, nrhs, x_diag, x_lower,
-                        x_arrow, x_tip, x_sol, h_logdet, w, prec, (cudaStream_t)stream);
+  PipeArgs io{};
+  io.host = true;
+  io.hd = h_diag; io.hl = h_lower; io.ha = h_arrow; io.ht = h_tip; io.hr = h_rhs;
+  io.xd = x_diag; io.xl = x_lower; io.xa = x_arrow; io.xt = x_tip; io.x = x_sol; io.hld = h_logdet;
+  return pipeline_impl(n, b, a, nrhs, io, w, prec, (cudaStream_t)stream);
+}
+
+size_t bta_all_workspace_bytes(int64_t n, int64_t b, int64_t a, int64_t nrhs) {
+  if (check_sizes(n, b, a) || nrhs < 0 || nrhs > 64) return 0;
+  return pipe_ws(n, b, a, nrhs, false, nullptr, nullptr, g_prec);
+}
+
+int bta_factor_selinv_all(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
+                          double* arrow, double* tip, double* rhs, int64_t nrhs, double* logdet_out,
+                          void* ws, size_t ws_bytes, bta_stream_t stream) {
+  int rc = check_sizes(n, b, a);
+  if (!rc) rc = check_blocks(n, a, diag, lower, arrow, tip);
+  if (rc) return rc;
+  if (nrhs < 0 || nrhs > 64) return -9;
+  if (nrhs > 0 && (!rhs || misaligned(rhs))) return -8;
+  if (!logdet_out || misaligned(logdet_out)) return -10;
+  PipeWs w;
+  const int prec = g_prec;
+  const size_t need = pipe_ws(n, b, a, nrhs, false, ws, &w, prec);
+  if (!ws || ((uintptr_t)ws % kAlign)) return -11;
+  if (ws_bytes < need) return -12;
+  PipeArgs io{};
+  io.host = false;
+  io.dd = diag; io.dl = lower; io.da = arrow; io.dt = tip; io.dr = rhs; io.ld_dev = logdet_out;
+  return pipeline_impl(n, b, a, nrhs, io, w, prec, (cudaStream_t)stream);
 }
 
 int bta_probe_fp64_peak(double* out_dev, int64_t iters, double* flops,

@@ -1,4 +1,6 @@
-"""bta_factor_selinv_host: the whole sequence from host memory, copies overlapped.
+"""bta_factor_selinv_host / bta_factor_selinv_all: the whole per-matrix sequence
+in one call (from host memory with the copies overlapped, or on device buffers),
+the solve overlapped with the selected inversion's prologue.
 
 Checked against the oracle (X on the pattern, log det, solve) and against the
 device-buffer entry points, over the fused FP64 step (b >= 128), the small-b
@@ -61,3 +63,34 @@ def test_host_pipeline_twice_in_a_row_is_bitwise_repeatable():
     torch.cuda.synchronize()
     for a_, b_ in zip(o1, [x for x in o2 if x is not None]):
         assert torch.equal(a_, b_)
+
+
+@pytest.mark.parametrize("n,b,a,nrhs", [(4, 160, 5, 3), (3, 40, 2, 1), (2, 256, 0, 2), (1, 130, 9, 0)])
+def test_device_all_in_one_matches_separate_calls(n, b, a, nrhs):
+    d, l, ar, t = gen.make_bta(n, b, a, seed=200 + n + b + a)
+    r = gen.make_rhs(n, b, a, max(nrhs, 1), seed=9)
+    D, Lw, A, Tp = dev(d), dev(l), dev(ar), dev(t)
+    R = dev(r) if nrhs else None
+    ld = bta.factor_selinv_all(D, Lw, A, Tp, rhs=R)
+    torch.cuda.synchronize()
+    assert bta.get_info() == 0
+    F = oracle.pobtaf(d, l, ar, t)
+    assert worst_block_error((host(D), host(Lw), host(A), host(Tp)), oracle.pobtasi(F)) <= TOL
+    ldo = oracle.logdet(F)
+    assert abs(float(ld.item()) - ldo) <= TOL * max(1.0, abs(ldo))
+    if nrhs:
+        assert rel_fro(host(R), oracle.solve(F, r)) <= TOL
+    # bit-identical to the four separate calls
+    D2, L2, A2, T2 = dev(d), dev(l), dev(ar), dev(t)
+    bta.factor(D2, L2, A2, T2)
+    ld2 = bta.logdet(D2, T2)
+    if nrhs:
+        R2 = dev(r)
+        bta.solve(D2, L2, A2, T2, R2)
+    bta.selinv(D2, L2, A2, T2)
+    torch.cuda.synchronize()
+    for x1, x2 in ((D, D2), (Lw, L2), (A, A2), (Tp, T2)):
+        assert torch.equal(x1, x2)
+    assert float(ld.item()) == float(ld2.item())
+    if nrhs:
+        assert torch.equal(R, R2)
