@@ -171,7 +171,7 @@ cudaError_t trtri_hook(const GemmArgs& g, void* ctx, cudaStream_t s) {
 
 // Blocks of at least this order are factored by the cooperative step kernel (one
 // matrix at a time); smaller ones, and matrices of a batch running on concurrent
-// streams, use the panel-by-panel launches.
+// streams, use the panel-by-panel launches with TRTRI + products for the TRSMs.
 constexpr int64_t kCoopMinB = 128;
 
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
@@ -194,13 +194,35 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
     return 0;
   }
+  if (coop && b >= kCoopMinB) {
+    // Tensor-core modes: the step kernel factors the block column (POTRF and the
+    // panel solves of L_{i+1,i}, L_{n,i} in FP64); the Schur products go through
+    // gemm_run (tensor cores for the large ones).
+    for (int64_t i = 0; i < n; ++i) {
+      const bool nx = i + 1 < n;
+      double* Di = diag + i * bb;
+      double* Li = nx ? lower + i * bb : nullptr;
+      double* Ai = a > 0 ? arrow + i * a * b : nullptr;
+      BTA_TRY(factor_step_coop(Di, Li, nullptr, Ai, nullptr, nullptr, B, Aa, nx ? 1 : 0, i * b,
+                               w.coop, s, /*schur=*/0));
+      if (nx)  // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
+        BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
+                                  Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s));
+      if (a > 0) {
+        if (nx)  // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
+          BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
+                                    Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
+        // A_{n,n} -= L_{n,i} L_{n,i}^T
+        BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
+                                  tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, prec, s));
+      }
+    }
+    if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
+    return 0;
+  }
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
-    if (coop && b >= kCoopMinB)  // the fused step kernel on A_ii alone: one cooperative POTRF
-      BTA_TRY(factor_step_coop(Di, nullptr, nullptr, nullptr, nullptr, nullptr, B, 0, 0, i * b,
-                               w.coop, s));
-    else
-      BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+    BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
     HookCtx hc{tw, prec};
     BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
     if (i + 1 < n) {

@@ -67,12 +67,13 @@ constexpr int kStepMaxExtTiles = 3 * 1024;
 static_assert(1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int) <= kCoopScratch,
               "step scratch");
 // One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}
-// and L_{n,i} in place, and the Schur updates of A_{i+1,i+1}, A_{n,i+1} and the
-// tip (lower tiles). next == 0 for the last block (Lw, D1, Ar1 unused); a == 0:
-// no arrowhead. scratch: kCoopScratch bytes, 256-byte aligned.
+// and L_{n,i} in place, and (schur != 0) the Schur updates of A_{i+1,i+1},
+// A_{n,i+1} and the tip (lower tiles). next == 0 for the last block (Lw, D1, Ar1
+// unused); a == 0: no arrowhead; schur == 0: D1, Ar1 and tip are unused.
+// scratch: kCoopScratch bytes, 256-byte aligned.
 cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
                              double* tip, int b, int a, int next, long long info_row0,
-                             void* scratch, cudaStream_t s);
+                             void* scratch, cudaStream_t s, int schur = 1);
 // Reads and clears the timeout flag of the cooperative kernels' grid barriers.
 cudaError_t wait_error_read_reset(int* out);
 // Enqueues one CTA that waits on *flag_dev (never raised) for `polls` polls.

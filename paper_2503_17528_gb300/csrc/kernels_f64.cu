@@ -732,6 +732,7 @@ struct StepArgs {
   double* Ar1;  // A_{n,i+1} (a x b): updated; unused when next == 0
   double* tip;  // A_nn (a x a): lower tiles updated
   int b, a, nt, na, next;
+  int schur;       // 0: only block i's columns (no updates of D1, Ar1, tip)
   long long row0;  // 1-based global row of block i's first row, minus one
   CoopBar* bar;
   double* rdiag;  // [2][T]: 1 / L_jj of the current diagonal tile (by step parity)
@@ -944,8 +945,13 @@ __global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p
     }
     if (look && beside0) wait_flag_ge(p.lflag, k + 1);
     const int ncol = look ? m - 1 : 0;                 // category 1
-    const int tri0 = look ? k + 2 : k + 1, tm = E - tri0;
-    const int nupd = ncol + tm * (tm + 1) / 2;          // categories 1 + 2
+    const int tri0 = look ? k + 2 : k + 1;
+    // Category 2: the lower triangle over tri0..E-1, or without Schur updates
+    // only its columns of block i: a triangle over tri0..nt-1 and the rectangle
+    // of the later rows under it.
+    const int tm = p.schur ? E - tri0 : max(0, nt - tri0);
+    const int ntri = tm * (tm + 1) / 2;
+    const int nupd = ncol + ntri + (p.schur ? 0 : (E - nt) * tm);  // categories 1 + 2
     const int per = 2, sh = T / per;                    // category 3: 16-row slices
     const int nitems = nupd + (look ? per * (m - 1) : 0);
     int* ctr = p.ctr + k;
@@ -953,10 +959,14 @@ __global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p
       if (t < ncol) {
         r = k + 2 + t;
         c = k + 1;
-      } else if (t < nupd) {
+      } else if (t < ncol + ntri) {
         const int u = t - ncol, rr = tri_row(u);
         r = tri0 + rr;
         c = tri0 + (u - rr * (rr + 1) / 2);
+      } else if (t < nupd) {
+        const int u = t - ncol - ntri;
+        r = nt + u / tm;
+        c = tri0 + u % tm;
       } else {
         const int sidx = t - nupd;
         r = k + 2 + sidx / per;
@@ -1097,10 +1107,11 @@ static double step_flops(double b, double a, int next) {
 
 cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
                              double* tip, int b, int a, int next, long long info_row0,
-                             void* scratch, cudaStream_t s) {
+                             void* scratch, cudaStream_t s, int schur) {
   StepArgs p;
   p.D0 = D0; p.Lw = Lw; p.D1 = D1; p.Ar0 = Ar0; p.Ar1 = Ar1; p.tip = tip;
   p.b = b; p.a = a; p.nt = (b + T - 1) / T; p.na = (a + T - 1) / T; p.next = next ? 1 : 0;
+  p.schur = schur ? 1 : 0;
   p.row0 = info_row0;
   p.bar = (CoopBar*)scratch;
   p.rdiag = (double*)((char*)scratch + 256);
@@ -1109,7 +1120,8 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
   p.ctr = (int*)((char*)scratch + 1024);
   p.colflag = p.ctr + kStepMaxTiles;
   if (p.nt > kStepMaxTiles || 2 * p.nt + p.na > kStepMaxExtTiles) return cudaErrorInvalidValue;
-  if (b < 1 || a < 0 || (next && (!Lw || !D1 || (a > 0 && !Ar1))) || (a > 0 && (!Ar0 || !tip)))
+  if (b < 1 || a < 0 || (next && !Lw) || (a > 0 && !Ar0) ||
+      (schur && ((next && (!D1 || (a > 0 && !Ar1))) || (a > 0 && !tip))))
     return cudaErrorInvalidValue;
   cudaError_t e =
       cudaMemsetAsync(scratch, 0, 1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int), s);
@@ -1543,15 +1555,25 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t ld
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (int k = lane; k < K; k += 32) {
+    double acc2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc2[q] = 0.0;
+    // Two k-steps per pass with separate sums: twice the loads in flight and
+    // half the dependent chain; the two sums are added in a fixed order.
+    for (int k = lane; k < K; k += 64) {
       const double av = A[(int64_t)row * lda + k];
+      const bool two = k + 32 < K;
+      const double av2 = two ? A[(int64_t)row * lda + k + 32] : 0.0;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (q < rc) acc[q] += av * y[(int64_t)k * ldy + r0 + q];
+        if (q < rc) {
+          acc[q] = fma(av, y[(int64_t)k * ldy + r0 + q], acc[q]);
+          if (two) acc2[q] = fma(av2, y[(int64_t)(k + 32) * ldy + r0 + q], acc2[q]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      double v = acc[q];
+      double v = acc[q] + acc2[q];
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       acc[q] = v;
     }
@@ -1595,14 +1617,78 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const double* A, int64_t ld
   }
 }
 
+// x[M][R] += alpha * A^T y (A stored K x M), R <= 8: a cluster of kGemvSplit
+// CTAs per 32 output rows splits k; in each CTA 8 warps split its k-range
+// (lane = row), the warps' sums are added in a fixed order in shared memory, and
+// rank 0 adds the CTAs' sums in rank order from distributed shared memory.
+constexpr int kGemvSplit = 4;
+
+__global__ void __launch_bounds__(256) gemv_t_split_kernel(const double* A, int64_t lda, int M, int K,
+                                                          const double* y, int64_t ldy, double* x,
+                                                          int64_t ldx, int R, double alpha) {
+  __shared__ double red[8][32][8];
+  __shared__ double part_sum[32][8];
+  unsigned part;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(part));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row = (blockIdx.x / kGemvSplit) * 32 + lane;
+  const int kq = (K + kGemvSplit - 1) / kGemvSplit, kp0 = (int)part * kq, kp1 = min(K, kp0 + kq);
+  const int kchunk = (kp1 - kp0 + 7) / 8, kb = kp0 + w * kchunk, ke = min(kp1, kb + kchunk);
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  if (row < M)
+    for (int k = kb; k < ke; ++k) {
+      const double av = A[(int64_t)k * lda + row];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < R) acc[q] = fma(av, y[(int64_t)k * ldy + q], acc[q]);
+    }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) red[w][lane][q] = acc[q];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = 0.0;
+      for (int ww = 0; ww < 8; ++ww) v += red[ww][lane][q];
+      part_sum[lane][q] = v;
+    }
+  }
+  cluster_sync_all();
+  if (part == 0 && w == 0 && row < M) {
+    for (int q = 0; q < R; ++q) {
+      double v = part_sum[lane][q];
+      for (unsigned p = 1; p < kGemvSplit; ++p) v += ld_dsmem(&part_sum[lane][q], p);
+      x[(int64_t)row * ldx + q] += alpha * v;
+    }
+  }
+  cluster_sync_all();  // the partial sums stay readable until rank 0 is done
+}
+
 cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K, const double* y,
                        int64_t ldy, double* x, int64_t ldx, int R, double alpha, cudaStream_t s) {
   if (M <= 0 || K <= 0 || R <= 0) return cudaSuccess;
   TimedLaunch tl(K_GEMV, 2.0 * M * K * R, s);
-  if (opA == OP_N)
+  if (opA == OP_N) {
     gemv_n_kernel<<<ceil_div(M, 8), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
-  else
-    gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
+    return cudaGetLastError();
+  }
+  if (R <= 8 && K >= 8 * kGemvSplit) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ceil_div(M, 32) * kGemvSplit);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGemvSplit;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemv_t_split_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha);
+  }
+  gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
   return cudaGetLastError();
 }
 
