@@ -173,6 +173,13 @@ cudaError_t trtri_hook(const GemmArgs& g, void* ctx, cudaStream_t s) {
 // matrix at a time); smaller ones, and matrices of a batch running on concurrent
 // streams, use the panel-by-panel launches with TRTRI + products for the TRSMs.
 constexpr int64_t kCoopMinB = 128;
+// In the tensor-core modes, blocks up to this order solve their panels in FP64
+// inside the step kernel (n=365, b=1024: Ozaki factor 907 ms against 998 ms with
+// TRTRI + tensor-core TRMM). Larger ones do so only where the TRSM products would
+// run in FP64 anyway (BF16x3; n=256, b=2048: 3.45 s against 4.66 s); with Ozaki
+// they take the inverse + tensor-core product, whose cost grows slower than the
+// FP64 solve's b^3 (n=256, b=2048: 2.07 s against 3.64 s).
+constexpr int64_t kHybridMaxB = 1024;
 
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
                 double* tip, const FactorWs& w, int prec, cudaStream_t s, bool coop = true) {
@@ -194,7 +201,7 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
     return 0;
   }
-  if (coop && b >= kCoopMinB) {
+  if (coop && b >= kCoopMinB && (b <= kHybridMaxB || !routes_to_tc(prec, CLS_TRSM))) {
     // Tensor-core modes: the step kernel factors the block column (POTRF and the
     // panel solves of L_{i+1,i}, L_{n,i} in FP64); the Schur products go through
     // gemm_run (tensor cores for the large ones).
@@ -222,7 +229,11 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   }
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
-    BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+    if (coop && b >= kCoopMinB)  // the step kernel on A_ii alone: one cooperative POTRF
+      BTA_TRY(factor_step_coop(Di, nullptr, nullptr, nullptr, nullptr, nullptr, B, 0, 0, i * b,
+                               w.coop, s));
+    else
+      BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
     HookCtx hc{tw, prec};
     BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
     if (i + 1 < n) {

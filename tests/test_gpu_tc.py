@@ -74,7 +74,7 @@ def test_gemm_zero_and_nan_rows():
     assert np.all(got[0] == 0) and np.allclose(got[7], 2.0)
 
 
-@pytest.mark.parametrize("n,b,a", [(6, 256, 8), (4, 300, 20), (3, 1024, 8), (2, 130, 0), (5, 64, 70)])
+@pytest.mark.parametrize("n,b,a", [(6, 256, 8), (4, 300, 20), (3, 1024, 8), (2, 1100, 4), (2, 130, 0), (5, 64, 70)])
 def test_ozaki_factor_selinv_parity(n, b, a):
     bta.set_precision("ozaki")
     d, l, ar, t = gen.make_bta(n, b, a, seed=n + b + a, shift=gen.SHIFT_1_01)
