@@ -68,3 +68,37 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.bta_factor_ws(2, 4, 1, good, good, good, good, None, 0, None) == -8
     assert lib.bta_factor_ws(2, 4, 1, good, good, good, good, v(4096), 16, None) == -9
     assert lib.bta_get_info(None, None) == -2
+
+
+def test_one_call_forms_check_arguments_before_the_gpu(lib):
+    v = ctypes.c_void_p
+    good = v(4096)
+    n, b, a = 3, 200, 4
+    # workspace sizes: the device form holds the scratch only, the host form adds
+    # the device copy of the pattern and the right-hand sides
+    dw = lib.bta_all_workspace_bytes(n, b, a, 2)
+    hw = lib.bta_host_pipeline_workspace_bytes(n, b, a, 2)
+    pattern = 8 * (n * b * b + (n - 1) * b * b + n * a * b + a * a + (n * b + a) * 2)
+    assert dw > 0 and hw >= dw + pattern
+    assert lib.bta_all_workspace_bytes(n, b, a, 65) == 0
+    assert lib.bta_host_pipeline_workspace_bytes(0, b, a, 1) == 0
+    # device form: rhs, logdet and workspace checks
+    assert lib.bta_factor_selinv_all(n, b, a, good, good, good, good, None, 1, good, good, dw, None) == -8
+    assert lib.bta_factor_selinv_all(n, b, a, good, good, good, good, good, 65, good, good, dw, None) == -9
+    assert lib.bta_factor_selinv_all(n, b, a, good, good, good, good, None, 0, None, good, dw, None) == -10
+    assert lib.bta_factor_selinv_all(n, b, a, good, good, good, good, None, 0, good, v(4100), dw,
+                                     None) == -11
+    assert lib.bta_factor_selinv_all(n, b, a, good, good, good, good, None, 0, good, good, 16, None) == -12
+    # host form: each host pointer is checked in argument order
+    args = [n, b, a, good, good, good, good, good, 2, good, good, good, good, good, good, good, hw, None]
+    assert lib.bta_factor_selinv_host(*args[:3], None, *args[4:]) == -4
+    assert lib.bta_factor_selinv_host(*args[:4], None, *args[5:]) == -5
+    assert lib.bta_factor_selinv_host(*args[:7], None, *args[8:]) == -8
+    assert lib.bta_factor_selinv_host(*args[:9], None, *args[10:]) == -10
+    assert lib.bta_factor_selinv_host(*args[:14], None, *args[15:]) == -15
+    assert lib.bta_factor_selinv_host(*args[:15], v(4100), *args[16:]) == -16
+    assert lib.bta_factor_selinv_host(*args[:16], 16, None) == -17
+    # the wait self-test's own checks
+    t = ctypes.c_int(0)
+    assert lib.bta_wait_selftest(0, ctypes.byref(t)) == -1
+    assert lib.bta_wait_selftest(10, None) == -2
