@@ -78,6 +78,14 @@ def measured_peaks():
                 "source": "profiling-recipe fallback"}
 
 
+def solve_bytes(n, b, a, nrhs):
+    """Algorithmic bytes of one solve: each sweep reads the factor once (lower
+    triangles of the diagonal blocks and of the tip, full off-diagonal and arrow
+    blocks) and reads and writes the right-hand sides once."""
+    factor = n * b * (b + 1) // 2 + (n - 1) * b * b + n * a * b + a * (a + 1) // 2
+    return 8 * (2 * factor + 4 * (n * b + a) * nrhs)
+
+
 def pattern_bytes(n, b, a):
     return 8 * (n * b * b + (n - 1) * b * b + n * a * b + a * a)
 
@@ -648,6 +656,13 @@ def run_ours(args, w, rank, world, local_rank):
             "fp64_peak_tflops_measured": round(peak_tf, 4),
             "frac_of_fp64_peak": round(tflops / peak_tf, 4),
             "roofline": roofline_of(stats, args.precision, peak_tf, peaks),
+            # the solve (a sequential chain of latency-bound triangular solves) against HBM
+            "solve_roofline": {
+                "bound": "latency", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                "achieved": round(solve_bytes(n, b, a, NRHS) / (phases["solve"] * 1e-3) / 1e9, 2),
+                "frac": round(solve_bytes(n, b, a, NRHS) / (phases["solve"] * 1e-3) / 1e9
+                              / peaks["hbm_gbs"], 4),
+                "traffic": None, "peak_source": peaks["source"]},
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()},
             "kernel_total_ms_per_step": round(total_kernel_ms, 3),
             "phase_ms": phases,
