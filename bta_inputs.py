@@ -101,3 +101,54 @@ def gram_of_factor_blocks(fd, fl, fa, ft):
         arrow[1:] += np.einsum("nij,nkj->nik", fa[:-1], fl)
     tip = np.einsum("nij,nkj->ik", fa, fa) + ft @ ft.T if a else np.zeros((0, 0))
     return diag, lower, arrow, tip
+
+
+def _assemble_symmetric(diag, lower, arrow, tip):
+    """Dense N x N symmetric matrix with the given blocks (input construction)."""
+    n, b = diag.shape[0], diag.shape[1]
+    a = tip.shape[0]
+    N = n * b + a
+    A = np.zeros((N, N))
+    for i in range(n):
+        A[i * b:(i + 1) * b, i * b:(i + 1) * b] = diag[i]
+        if i + 1 < n:
+            A[(i + 1) * b:(i + 2) * b, i * b:(i + 1) * b] = lower[i]
+            A[i * b:(i + 1) * b, (i + 1) * b:(i + 2) * b] = lower[i].T
+        if a:
+            A[n * b:, i * b:(i + 1) * b] = arrow[i]
+            A[i * b:(i + 1) * b, n * b:] = arrow[i].T
+    if a:
+        A[n * b:, n * b:] = tip
+    return A
+
+
+def make_bta_stress(n: int, b: int, a: int, seed: int = 0, kappa: float = 1e6):
+    """A badly conditioned SPD BTA matrix for error statements of the reduced-
+    precision modes (the dominance-shifted generator gives condition numbers of
+    only 3 to 8). The blocks are drawn as in make_bta, without the dominance
+    shift; then every diagonal entry gets the shift s that sets the spectral
+    condition number of the whole matrix to `kappa`:
+    (lambda_max + s) / (lambda_min + s) = kappa, with lambda_min, lambda_max the
+    extreme eigenvalues of the random symmetric part. Dense eigenvalues: for
+    N = n*b + a up to 6000. Returns (diag, lower, arrow, tip, kappa_achieved).
+    """
+    if n < 1 or b < 1 or a < 0:
+        raise ValueError("need n >= 1, b >= 1, a >= 0")
+    if n * b + a > 6000:
+        raise ValueError("make_bta_stress computes dense eigenvalues: N = n*b + a must be <= 6000")
+    if not kappa > 1.0:
+        raise ValueError("kappa must exceed 1")
+    rng = np.random.default_rng(seed)
+    s = 1.0 / np.sqrt(b)
+    diag = _symmetric_from_lower(rng.standard_normal((n, b, b)) * s)
+    lower = rng.standard_normal((n - 1, b, b)) * s
+    arrow = rng.standard_normal((n, a, b)) * s
+    tip = _symmetric_from_lower(rng.standard_normal((a, a)) * s)
+    lam = np.linalg.eigvalsh(_assemble_symmetric(diag, lower, arrow, tip))
+    lo, hi = float(lam[0]), float(lam[-1])
+    shift = (hi - kappa * lo) / (kappa - 1.0)
+    idx = np.arange(b)
+    diag[:, idx, idx] += shift
+    if a:
+        tip[np.arange(a), np.arange(a)] += shift
+    return diag, lower, arrow, tip, (hi + shift) / (lo + shift)
