@@ -2,11 +2,14 @@
 """Benchmark of the BTA hot path on GB300: factor + log-det + solve + selected inversion.
 
 One step = one pass of the whole path over one synthetic BTA matrix resident in
-HBM: reset the working blocks from a pristine device copy, bta_factor,
-bta_logdet, bta_solve (4 right-hand sides), bta_selinv. The metric is ms per
-matrix (lower is better); TFLOP/s of the algorithmic FP64 flop count is reported
-beside it. Multi-GPU (torchrun): every rank factors and inverts its own matrix
-(independent problems, weak scaling, no collective on the data path).
+HBM: reset the working blocks from a pristine device copy, then factor, log-det,
+solve (4 right-hand sides) and selected inversion in one bta_factor_selinv_all
+call (the same results as bta_factor, bta_logdet, bta_solve, bta_selinv in a
+row). The metric is ms per matrix (lower is better); TFLOP/s of the algorithmic
+FP64 flop count is reported beside it. `e2e` times bta_factor_selinv_host from
+pinned host buffers (inputs in, X, x and log det out, inside the timed region).
+Multi-GPU (torchrun): every rank factors and inverts its own matrix (independent
+problems, weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
