@@ -4,7 +4,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace bta {
+
+// A launch parameter computed once per device (SM counts, occupancy, function
+// attributes). Thread-safe: callers racing on a device's first use may each
+// compute it, with the same result; 0 marks "not computed yet", so `compute`
+// must return a nonzero value. `compute` runs with that device current.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  std::atomic<long long> v[kMaxDevices];
+};
+template <class F>
+inline long long per_device(PerDevice& c, F compute) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
+  long long x = c.v[dev].load(std::memory_order_acquire);
+  if (x) return x;
+  x = compute();
+  c.v[dev].store(x, std::memory_order_release);
+  return x;
+}
 
 constexpr int T = 32;  // edge of every FP64 tile
 
@@ -48,6 +69,9 @@ inline GemmTerm term(const double* A, int64_t lda, int opA, int triA,
 }
 
 cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s);
+// Algorithmic flops of a GEMM call (2 per structurally non-zero multiply-add over
+// the outputs it defines, all batch entries); host-side, for the timing records.
+double gemm_alg_flops(const GemmArgs& g);
 
 // Dense block kernels (all FP64, row-major, leading dimension ld; `count`
 // blocks at stride `sb` elements; square blocks of order `nrow`).

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs g, int ksplit) {
 // Algorithmic flops of one launch: 2 per multiply-add whose operands are not
 // structurally zero, over the output elements the call defines (all of C, or
 // its lower triangle for lowerC). Host-side, only evaluated when timing is on.
-static double gemm_alg_flops(const GemmArgs& g) {
+double gemm_alg_flops(const GemmArgs& g) {
   double total = 0.0;
   for (int ti = 0; ti < g.nterms; ++ti) {
     const GemmTerm& t = g.t[ti];
@@ -354,16 +354,17 @@ __global__ void __launch_bounds__(256) gemm_skinny_kernel(GemmArgs g) {
 // (mean over max CTAs per SM) while staying within one wave and keeping at least
 // 4 chunks per part. (Splitting past a wave measured slower: 1024 tiles of a
 // 1024 x 1024 x 1032 product took 2.21 ms split 4-way against 2.17 ms unsplit.)
+static PerDevice g_gemm_shape;
+
 static int gemm_ksplit(long long ctas, int kchunks) {
-  static int sms = 0, per_sm = 0;
-  if (!sms) {
-    int dev = 0;
+  const long long packed = per_device(g_gemm_shape, [] {
+    int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_f64_kernel, 128, 0);
-    if (sms < 1) sms = 1;
-    if (per_sm < 1) per_sm = 1;
-  }
+    return (long long)std::max(sms, 1) * 4096 + std::max(per_sm, 1);
+  });
+  const int sms = (int)(packed / 4096), per_sm = (int)(packed % 4096);
   const long long slots = (long long)sms * per_sm;
   if (ctas >= slots) return 1;
   auto eff = [&](long long n) {
@@ -427,12 +428,21 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
 // ~2^-23 seed error below FP64 rounding. Every dependent FP64 instruction is
 // expensive on this part, and this chain is about half the length of a
 // correctly rounded sqrt followed by a division; the pivot is then d * y.
+// A pivot outside the float range (binary exponent beyond +-100, or subnormal)
+// is first written d = d' 4^k with d' near 1 (exact power-of-two scaling), the
+// iteration runs on d', and y = y' 2^-k: an SPD matrix scaled by any power of
+// two factors like the unscaled one. Inf or NaN pivots are not rescaled and
+// come out NaN (0 * inf) in the pivot.
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  double y = (double)rsqrtf((float)d);
-  const double h = 0.5 * d;
+  const int e = (int)((__double_as_longlong(d) >> 52) & 0x7ff) - 1023;  // -1023: zero/subnormal
+  const int k = (e > 100 || e < -100) && e != 1024 ? e / 2 : 0;          // |k| <= 511
+  // 2^-2k and 2^-k as bit patterns: biased exponents 1023-2k in [1, 2045], 1023-k in [512, 1534].
+  const double ds = k ? d * __longlong_as_double((long long)(1023 - 2 * k) << 52) : d;
+  double y = (double)rsqrtf((float)ds);
+  const double h = 0.5 * ds;
   y = y * fma(-h * y, y, 1.5);
   y = y * fma(-h * y, y, 1.5);
-  return y;
+  return k ? y * __longlong_as_double((long long)(1023 - k) << 52) : y;
 }
 
 // One right-looking step k of a blocked Cholesky, fused: CTA 0 factors the
@@ -1082,24 +1092,29 @@ __global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p
   }
 }
 
+static PerDevice g_step_grid;
+
+// Cooperative grid of the step kernel on the current device (at most 2 CTAs per
+// SM, as many as are co-resident; -1 if none can be).
 static int step_grid() {
-  static int cached = -1;
-  if (cached < 0) {
+  return (int)per_device(g_step_grid, [] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_step_kernel, kStepThreads, 0);
     // Several CTAs per SM: one CTA's loads, stores and barriers overlap the
     // others' DMMA work on the SM's FP64 pipe.
-    cached = std::min(per, 2) * sms;
-  }
-  return cached;
+    const int g = std::min(per, 2) * sms;
+    return (long long)(g > 0 ? g : -1);
+  });
 }
 
 // Algorithmic flops of one step: POTRF b^3/3, the (b [+ b] + a)-row panel solve
-// (b^2 per row), and the Schur products on the lower triangles they update.
-static double step_flops(double b, double a, int next) {
+// (b^2 per row), and (schur != 0) the Schur products on the lower triangles they
+// update; without them the launch does only the POTRF and the panel solves.
+static double step_flops(double b, double a, int next, int schur) {
   double f = b * b * b / 3.0 + (next ? b : 0.0) * b * b + a * b * b;
+  if (!schur) return f;
   if (next) f += b * (b + 1) * b + 2.0 * a * b * b;
   f += a * (a + 1) * b;
   return f;
@@ -1129,7 +1144,7 @@ cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, do
   const int G = step_grid();
   if (G < 2) return cudaErrorInvalidConfiguration;
   void* args[] = {&p};
-  TimedLaunch tl(K_FACTOR_STEP, timing_on() ? step_flops(b, a, p.next) : 0.0, s);
+  TimedLaunch tl(K_FACTOR_STEP, timing_on() ? step_flops(b, a, p.next, p.schur) : 0.0, s);
   return cudaLaunchCooperativeKernel((void*)factor_step_kernel, dim3(G), dim3(kStepThreads), args,
                                      0, s);
 }
@@ -1488,9 +1503,10 @@ __global__ void __launch_bounds__(256, 1) trsv_cluster_kernel(const double* L, i
   }
 }
 
+static PerDevice g_trsv_cluster;
+
 static int trsv_cluster_size(cudaStream_t s) {
-  static int chosen = 0;
-  if (chosen) return chosen;
+  return (int)per_device(g_trsv_cluster, [s]() -> long long {
   int sz = 16;
   if (cudaFuncSetAttribute(trsv_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
       cudaSuccess) {
@@ -1516,8 +1532,8 @@ static int trsv_cluster_size(cudaStream_t s) {
       sz = 8;
     }
   }
-  chosen = sz;
-  return chosen;
+  return sz;
+  });
 }
 
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t ldx, int R,

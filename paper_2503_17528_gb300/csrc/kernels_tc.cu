@@ -655,7 +655,7 @@ static void fill_op(SplitOp* op, const Part* parts, int np, int nb1, int zbase, 
   }
 }
 
-static int g_smem_attr_set = 0;
+static PerDevice g_tc_dyn_limit;
 
 cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (g.nterms < 1 || g.nterms > kMaxTerms) return cudaErrorInvalidValue;
@@ -701,30 +701,27 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
   if (chunk_nb > total) chunk_nb = total;
   while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) --chunk_nb;
   if (tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
-  // Dynamic shared memory: the opt-in limit less the kernel's static shared memory.
-  static size_t dyn_limit = 0;
-  if (!dyn_limit) {
+  // Dynamic shared memory: the opt-in limit less the kernel's static shared
+  // memory, raised on the kernel once per device (-1: the query failed).
+  const long long dyn_limit = per_device(g_tc_dyn_limit, []() -> long long {
     int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, tc_gemm_kernel);
-    if (e != cudaSuccess) return e;
-    dyn_limit = (size_t)optin - fa.sharedSizeBytes;
-  }
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, tc_gemm_kernel) != cudaSuccess)
+      return -1;
+    const long long lim = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (lim <= 0 || cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)lim) != cudaSuccess)
+      return -1;
+    return lim;
+  });
+  if (dyn_limit < 0) return cudaErrorInvalidConfiguration;
   const uint32_t stage_bytes = (uint32_t)S * (BM + BN) * BK * 2;
   int nstages = (int)((dyn_limit - 1024) / stage_bytes);
   if (nstages > kMaxStages) nstages = kMaxStages;
   if (nstages < 1) return cudaErrorInvalidValue;
   const size_t smem = (size_t)nstages * stage_bytes + 1024;
-  if ((size_t)g_smem_attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    g_smem_attr_set = (int)smem;
-  }
   const int unitk = mode == TC_OZ ? kUnitK : Kp;
   const int nunits = (Kp + unitk - 1) / unitk;
   const GemmTerm& t0 = g.t[0];
@@ -774,9 +771,9 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     a.alpha = t0.alpha; a.beta = g.beta;
     const long long grid = (long long)(Mp / BM) * (Np / BN) * nunits * nb;
     {
-      double fl = 0.0;
-      for (int i = 0; i < g.nterms; ++i) fl += 2.0 * M * N * (double)g.t[i].K;
-      TimedLaunch tl(K_GEMM_TC, fl * nb * (g.lowerC && M == N ? 0.5 : 1.0), s);
+      // algorithmic flops of this chunk's nb batch entries
+      const double fl = timing_on() ? gemm_alg_flops(g) / total * nb : 0.0;
+      TimedLaunch tl(K_GEMM_TC, fl, s);
       tc_gemm_kernel<<<(unsigned)grid, kThreads, smem, s>>>(mA, mB, a);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;

@@ -159,3 +159,39 @@ def test_n365_b1024_a8_full_parity():
     bta.selinv(D, Lo, Ar, Ti)
     Xo = oracle.pobtasi(F)
     assert worst_block_error([host(x) for x in (D, Lo, Ar, Ti)], Xo) <= TOL
+
+
+@pytest.mark.parametrize("b", [40, 160])
+@pytest.mark.parametrize("e", [140, -160])
+def test_power_of_two_scaled_matrix(b, e):
+    """A matrix scaled by 2^140 (pivots above the float range) or 2^-160 (below
+    it) factors, inverts and solves like the unscaled one: L scales by 2^(e/2),
+    X by 2^-e, exactly. Covers the step kernel (b = 160), the panel kernel
+    (b = 40) and the tip."""
+    n, a = 3, 5
+    d, l, ar, t = gen.make_bta(n, b, a, seed=21 + b)
+    s = 2.0 ** e
+    d, l, ar, t = d * s, l * s, ar * s, t * s
+    (d, l, ar, t, r), Lg, ldg, xg, Xg = _run_scaled(d, l, ar, t, seed=22)
+    F = oracle.pobtaf(d, l, ar, t)
+    assert F.info == 0 and bta.get_info() == 0
+    assert np.isfinite(Lg[0]).all() and np.isfinite(Xg[0]).all()
+    assert worst_block_error(Lg, (F.diag, F.lower, F.arrow, F.tip)) <= TOL
+    ldo = oracle.logdet(F)
+    assert abs(ldg - ldo) <= TOL * abs(ldo)
+    assert rel_fro(xg, oracle.solve(F, r)) <= TOL
+    assert worst_block_error(Xg, oracle.pobtasi(F)) <= TOL
+
+
+def _run_scaled(d, l, ar, t, seed):
+    n, b, a = d.shape[0], d.shape[1], t.shape[0]
+    D, Lo, Ar, Ti = dev(d), dev(l), dev(ar), dev(t)
+    bta.factor(D, Lo, Ar, Ti)
+    ld = bta.logdet(D, Ti)
+    r = gen.make_rhs(n, b, a, nrhs=2, seed=seed)
+    R = dev(r)
+    bta.solve(D, Lo, Ar, Ti, R)
+    Lg = [host(x) for x in (D, Lo, Ar, Ti)]
+    bta.selinv(D, Lo, Ar, Ti)
+    torch.cuda.synchronize()
+    return (d, l, ar, t, r), Lg, float(ld.item()), host(R), [host(x) for x in (D, Lo, Ar, Ti)]
