@@ -151,10 +151,13 @@ int bta_logdet_ws(int64_t n, int64_t b, int64_t a, const double* diag,
  * until the process exits. The paper has no counterpart; this is an interface
  * convenience.
  * Limits: n <= 65536 (larger n returns -1, nothing is enqueued).
+ * `stream` must belong to the current device (else -7, nothing enqueued).
  * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture. All calls on
- * a device share the array: calls that overlap on the GPU race and must be
- * ordered by the caller (same stream, or events).
+ * device current); make that first call before any stream capture. The address
+ * is kept for the life of the process, so do not call this entry point on a
+ * device after cudaDeviceReset there. All calls on a device share the array:
+ * calls that overlap on the GPU race and must be ordered by the caller (same
+ * stream, or events).
  */
 int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double* diag,
                        const double* tip, double* out_dev, bta_stream_t stream);

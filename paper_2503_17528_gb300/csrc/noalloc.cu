@@ -15,7 +15,10 @@
 // device current). All calls on a device share the one array and it keeps the
 // last call's contents; each call overwrites every partial it later reads, so
 // nothing has to start at zero, but calls that overlap on the GPU (different
-// streams, no ordering between them) race on the array.
+// streams, no ordering between them) race on the array. The looked-up address
+// is kept for the life of the process: a cudaDeviceReset on a device unloads the
+// library's module there, so a process that resets a device must not call this
+// entry point on that device afterwards.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,16 +36,14 @@ static __device__ __align__(256) double g_logdet_scratch[kMaxBlocks + 1];
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_logdet_scratch on the current device (looked up once).
-cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of g_logdet_scratch on device `dev` (looked up once per
+// device, with that device current).
+cudaError_t scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_logdet_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_logdet_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = (double*)p;
   }
@@ -60,8 +61,20 @@ extern "C" int bta_logdet_noalloc(int64_t n, int64_t b, int64_t a, const double*
   if (!diag || ((uintptr_t)diag & 7u)) return -4;
   if (a > 0 && (!tip || ((uintptr_t)tip & 7u))) return -5;
   if (!out_dev || ((uintptr_t)out_dev & 7u)) return -6;
+  // The scratch address is per device: the one the kernel runs on is the
+  // stream's, which must be the current device (a kernel cannot be launched
+  // into another device's stream).
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (stream) {
+    int sdev = -1;
+    e = cudaStreamGetDevice((cudaStream_t)stream, &sdev);
+    if (e != cudaSuccess) return (int)e;
+    if (sdev != dev) return -7;
+  }
   double* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  e = scratch_address(dev, &scratch);
   if (e != cudaSuccess) return (int)e;
   e = bta::logdet_f64(diag, n, b, tip, a, scratch, out_dev, (cudaStream_t)stream);
   return e == cudaSuccess ? 0 : (int)e;

@@ -47,6 +47,30 @@ def test_noalloc_logdet_matches_logdet_on_two_calls():
         assert abs(g - r) <= TOL * max(1.0, abs(r)), (n, g, r)
 
 
+@pytest.mark.parametrize("a", [1, 0])
+def test_noalloc_logdet_at_the_block_limit(a):
+    """n = 65536 fills the fixed array to its last slot (n partial sums, plus one
+    for the tip when a > 0). Log-det only reads the diagonals of the factor's
+    blocks, so a positive-diagonal stand-in for the factor serves as input."""
+    lib = _lib.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda x: ctypes.c_void_p(x.data_ptr())  # noqa: E731
+    n, b = 65536, 1
+    rng = np.random.default_rng(11 + a)
+    D = torch.from_numpy(rng.uniform(0.5, 2.0, (n, b, b))).to("cuda")
+    Ti = torch.from_numpy(rng.uniform(0.5, 2.0, (a, a))).to("cuda")
+    tip = p(Ti) if a else None
+    for _ in range(2):
+        ref = torch.empty((), dtype=torch.float64, device="cuda")
+        got = torch.full((), np.nan, dtype=torch.float64, device="cuda")
+        assert lib.bta_logdet(n, b, a, p(D), tip, p(ref), stream) == 0
+        assert lib.bta_logdet_noalloc(n, b, a, p(D), tip, p(got), stream) == 0
+        torch.cuda.synchronize()
+        r, g = ref.item(), got.item()
+        assert np.isfinite(g) and abs(g - r) <= TOL * max(1.0, abs(r)), (g, r)
+        D.mul_(1.5)  # the second call sees other values in every slot
+
+
 def test_noalloc_logdet_rejects_too_many_blocks():
     lib = _lib.load()
     dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
