@@ -95,7 +95,9 @@ def test_ozaki_factor_selinv_parity(n, b, a):
 
 
 def test_bf16x3_mixed_error_is_bounded():
-    """Mixed precision: stated bound on the per-block error against the FP64 oracle."""
+    """Mixed precision: stated bound on the per-block error against the FP64 oracle,
+    4 kappa u with u = 2^-16 (split-BF16x3 products) and kappa <= 4 for this
+    generator (1.001 dominance shift, measured kappa about 3): 2.4e-4."""
     bta.set_precision("bf16x3")
     n, b, a = 6, 256, 8
     d, l, ar, t = gen.make_bta(n, b, a, seed=5, shift=gen.SHIFT_1_001)
@@ -105,5 +107,6 @@ def test_bf16x3_mixed_error_is_bounded():
     bta.selinv(D, Lo, Ar, Ti)
     torch.cuda.synchronize()
     F = oracle.pobtaf(d, l, ar, t)
-    assert worst_block_error(Lg, (F.diag, F.lower, F.arrow, F.tip)) <= 1e-3
-    assert worst_block_error([host(x) for x in (D, Lo, Ar, Ti)], oracle.pobtasi(F)) <= 1e-3
+    bound = 4 * 4.0 * 2.0 ** -16
+    assert worst_block_error(Lg, (F.diag, F.lower, F.arrow, F.tip)) <= bound
+    assert worst_block_error([host(x) for x in (D, Lo, Ar, Ti)], oracle.pobtasi(F)) <= bound
