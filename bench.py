@@ -13,13 +13,18 @@ problems, weak scaling, no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
-Default workload: n=365, b=1024, a=8, dominance shift 1.01 (inputs ~6.1 GB, far
-above the 129 MB L2, so no L2 flush is needed between steps).
+Default workload: n=256, b=2048, a=16, dominance shift 1.001 (inputs 17.2 GB, far
+above the 129 MB L2, so no L2 flush is needed between steps). Beside the FP64
+line: the tensor-core precision modes on the same matrix (speedup and per-block
+error against the FP64 result), and the batched form (64 uneven matrices, one
+call replayed from a CUDA graph, against 64 sequential plain FP64 calls, with a
+sample checked against the oracle). Wall-clock progress goes to stderr.
 """
 from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import os
 import statistics
@@ -79,6 +84,32 @@ def measured_peaks():
     except (OSError, KeyError, ValueError):
         return {"bf16_burst": 1900.0, "bf16_sustained": 1700.0, "hbm_gbs": 6800.0,
                 "source": "profiling-recipe fallback"}
+
+
+# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum, summed over the kernel's launches of one step in one ncu
+# capture and divided by their number), keyed by kernel name. Each entry names
+# the source file the kernel lives in and a digest of that file at capture time:
+# once the source changes, the figure no longer describes the kernel and the
+# bench line reports traffic as null.
+TRAFFIC = {}
+
+
+def _source_digest(rel):
+    with open(os.path.join(ROOT, "paper_2503_17528_gb300", "csrc", rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_of(kernel, workload):
+    e = TRAFFIC.get(kernel)
+    if not e or e.get("workload") != workload:
+        return None
+    try:
+        if _source_digest(e["source"]) != e["digest"]:
+            return None
+    except OSError:
+        return None
+    return {"bytes_per_launch": e["bytes_per_launch"], "capture": e["capture"]}
 
 
 def solve_bytes(n, b, a, nrhs):
@@ -166,14 +197,17 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(w, arrays, target_s=8.0, max_blocks=None):
-    """Time the oracle (factor, logdet, solve, selinv) on leading principal block
-    sub-matrices of the workload, doubling the block count until one run takes
-    >= target_s. Returns (ms per full matrix, sample description, cores)."""
+def cpu_oracle_sample(w, arrays, target_s=8.0, max_blocks=None, ns_fixed=None):
+    """Time the oracle (factor, logdet, solve, selinv) on a leading principal block
+    sub-matrix of the workload (the first ns block rows plus the arrowhead, itself
+    an SPD BTA matrix), doubling ns until one run takes >= target_s (or using
+    ns_fixed). Every block step of the method costs the same, so the full matrix
+    costs n/ns times the sample, up to the tip. Returns (ms per full matrix,
+    sample description, cores, ns, sample seconds)."""
     import oracle
     d, l, ar, t, r = arrays
     n, b, a = w["n"], w["b"], w["a"]
-    ns = min(n, 2)
+    ns = ns_fixed or min(n, 2)
     while True:
         rs = np.concatenate([r[: ns * b], r[n * b:]])
         t0 = time.perf_counter()
@@ -182,13 +216,13 @@ def cpu_oracle_sample(w, arrays, target_s=8.0, max_blocks=None):
         oracle.solve(F, rs)
         oracle.pobtasi(F)
         dt = time.perf_counter() - t0
-        if dt >= target_s or ns >= n or (max_blocks and ns >= max_blocks):
+        if ns_fixed or dt >= target_s or ns >= n or (max_blocks and ns >= max_blocks):
             break
         ns = min(n, ns * 2)
     per_full = dt * 1e3 * n / ns
     desc = (f"oracle (NumPy/SciPy FP64) on the leading {ns} of {n} block rows plus the arrowhead "
-            f"({dt:.1f} s), scaled by n/{ns} to one full matrix")
-    return per_full, desc, os.cpu_count()
+            f"({dt:.1f} s), scaled by n/{ns} to one full matrix (extrapolated, not run on the whole matrix)")
+    return per_full, desc, os.cpu_count(), ns, dt
 
 
 def rank_seed(rank: int) -> int:
@@ -227,19 +261,25 @@ def make_workload(w, seed):
 
 # ---------------------------------------------------------------------------
 def run_reference(args, w, rank, world):
+    """The reference arm: the oracle as it stands, on the host cores, on a bounded
+    sample of the workload per step (see cpu_oracle_sample). `ms_per_step` is the
+    time one step really took; `value` is that sample scaled to one full matrix."""
     if rank != 0:
         return 0
     arrays = make_workload(w, seed=0)
-    t_steps = []
-    desc = cores = None
+    per, secs = [], []
+    desc = cores = ns = None
     for i in range(args.warmup + args.steps):
-        per_full, desc, cores = cpu_oracle_sample(w, arrays, target_s=args.ref_target_s)
+        per_full, desc, cores, ns, dt = cpu_oracle_sample(w, arrays, target_s=args.ref_target_s, ns_fixed=ns)
         if i >= args.warmup:
-            t_steps.append(per_full)
-    v = statistics.median(t_steps)
+            per.append(per_full)
+            secs.append(dt)
+    v = statistics.median(per)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ms/matrix",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * statistics.median(secs), 3),
+        "value_is_extrapolated": f"each step runs the oracle on {ns} of {w['n']} block rows; value = n/{ns} x that",
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(w),
         "cpu_baseline": {"value": round(v, 3), "unit": "ms/matrix", "cores": cores, "kind": "oracle",
@@ -263,19 +303,26 @@ def make_batch(count=64, seed=2026):
     return out
 
 
-def run_batch(args):
-    """Batched form: 64 sequential plain FP64 calls vs. one tuned batched call
-    replayed from a CUDA graph (the reset copy of the inputs is in both)."""
+def _log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def batch_measure(steps, warmup, dev, rank=0, world=1, oracle_sample=0, quick_tune=False):
+    """Batched form on this rank's shard of the 64-matrix batch: sequential plain
+    FP64 calls against one tuned batched call replayed from a CUDA graph (the
+    reset copy of the inputs is in both). Returns the measurements as a dict."""
     import torch
     import paper_2503_17528_gb300 as bta
     from paper_2503_17528_gb300 import tune
     from paper_2503_17528_gb300.batched import Batch
-    dev = torch.device("cuda", 0)
-    raw = make_batch()
+    raw_all = make_batch()
+    fl_all = [flops_factor(m[0].shape[0], m[0].shape[1], m[3].shape[0]) +
+              flops_selinv(m[0].shape[0], m[0].shape[1], m[3].shape[0]) for m in raw_all]
+    mine = sorted(shard_batch(fl_all, world)[rank])
+    raw = [raw_all[k] for k in mine]
+    flops = sum(fl_all[k] for k in mine)
     P = [tuple(torch.from_numpy(x).to(dev) for x in m) for m in raw]
     W = [tuple(x.clone() for x in m) for m in P]
-    flops = sum(flops_factor(m[0].shape[0], m[0].shape[1], m[3].shape[0]) +
-                flops_selinv(m[0].shape[0], m[0].shape[1], m[3].shape[0]) for m in raw)
 
     def reset():
         for w, p in zip(W, P):
@@ -294,60 +341,98 @@ def run_batch(args):
             bta.selinv(d, l, ar, t)
 
     def timed(fn, k):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
-        torch.cuda.synchronize()
+        torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(k):
             fn()
         e1.record()
-        torch.cuda.synchronize()
+        torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / k
 
-    seq_ms = timed(sequential, args.steps)
+    seq_ms = timed(sequential, steps)
     seq_out = [tuple(x.clone() for x in w) for w in W]
+    seq_ld = lds.clone()
     cfg = tune.lookup(W)
     tuned_now = cfg is None
     if cfg is None:
-        cfg = tune.tune(W, P)
+        if quick_tune:
+            cfg = tune.tune(W, P, policies=["fp64", "ozaki_b256"], streams=(8, 16), reps=1, save=False)
+        else:
+            cfg = tune.tune(W, P)
     batch = Batch(W, policy=cfg["policy"], nstreams=cfg["nstreams"])
     reset()
     batch.run()
-    torch.cuda.synchronize()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
         graph = batch.capture()
-    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.current_stream(dev).wait_stream(side)
 
     def replay():
         reset()
         graph.replay()
 
-    graph_ms = timed(replay, args.steps)
+    graph_ms = timed(replay, steps)
     worst = 0.0
     for w, r in zip(W, seq_out):
         for x, y in zip(w, r):
             if y.numel():
-                num = torch.linalg.norm((x - y).flatten(1) if x.dim() == 3 else (x - y).flatten(0)[None], dim=1)
-                den = torch.linalg.norm(y.flatten(1) if y.dim() == 3 else y.flatten(0)[None], dim=1)
-                worst = max(worst, float((num / den.clamp_min(1e-300)).max()))
-    line = {"metric": "BTA batched factor+logdet+selinv ms/batch (64 uneven matrices)",
-            "value": round(graph_ms, 3), "unit": "ms/batch", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(graph_ms, 3), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if cfg["policy"] == "fp64" else
-            "f64 + bf16-slice FP64 emulation (b >= 256)" if cfg["policy"] == "ozaki_b256" else "bf16 slices (FP64-emulated)",
-            "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "matrices": len(raw), "total_flops": flops,
-                       "steps_include": "device reset copy + all 64 matrices"},
-            "sequential_plain_fp64_ms": round(seq_ms, 3), "speedup_vs_sequential": round(seq_ms / graph_ms, 3),
-            "tflops_per_gpu": round(flops / (graph_ms * 1e-3) / 1e12, 4),
-            "tuned": {k: cfg[k] for k in ("nstreams", "policy", "ms")}, "tuned_in_this_run": tuned_now,
-            "tuning_table": cfg.get("table"),
-            "max_block_rel_err_vs_sequential_fp64": float(f"{worst:.3e}")}
-    print(json.dumps(line), flush=True)
+                worst = max(worst, blockerr(x, y))
+    out = {"ms_per_batch": round(graph_ms, 3), "matrices": len(raw), "total_flops": flops,
+           "sequential_plain_fp64_ms": round(seq_ms, 3), "speedup_vs_sequential": round(seq_ms / graph_ms, 3),
+           "tflops": round(flops / (graph_ms * 1e-3) / 1e12, 4),
+           "tuned": {k: cfg[k] for k in ("nstreams", "policy", "ms")}, "tuned_in_this_run": tuned_now,
+           "dtype": "f64" if cfg["policy"] == "fp64" else
+           "f64 + bf16-slice FP64 emulation (b >= 256)" if cfg["policy"] == "ozaki_b256"
+           else "bf16 slices (FP64-emulated)",
+           "max_block_rel_err_vs_sequential_fp64": float(f"{worst:.3e}")}
+    if oracle_sample:
+        # The first few matrices of the batched result against the oracle.
+        import oracle
+        ow = 0.0
+        ld_err = 0.0
+        logdets = batch.logdets.cpu().numpy()
+        for k in range(min(oracle_sample, len(raw))):
+            F = oracle.pobtaf(*raw[k])
+            X = oracle.pobtasi(F)
+            for x, y in zip(W[k], X):
+                if y.size:
+                    ow = max(ow, blockerr(x.cpu(), torch.from_numpy(y)))
+            ldo = oracle.logdet(F)
+            ld_err = max(ld_err, abs(float(logdets[k]) - ldo) / abs(ldo))
+        out["oracle_check"] = {"matrices": min(oracle_sample, len(raw)),
+                               "max_block_rel_err_vs_oracle": float(f"{ow:.3e}"),
+                               "max_logdet_rel_err_vs_oracle": float(f"{ld_err:.3e}")}
+    del seq_ld
+    return out
+
+
+def run_batch(args, rank=0, world=1, local_rank=0):
+    """The batched workload as its own bench line: each rank runs its shard of the
+    64 matrices (largest-first bin-pack on algorithmic flops, no data-path
+    collective); the job time is the slowest rank's."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    res = batch_measure(args.steps, args.warmup, dev, rank, world)
+    ms = max_over_ranks(res["ms_per_batch"], dist, dev)
+    if rank == 0:
+        line = {"metric": "BTA batched factor+logdet+selinv ms/batch (64 uneven matrices)",
+                "value": round(ms, 3), "unit": "ms/batch", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+                "scaling": "strong", "vs_baseline": None, "dtype": res["dtype"], "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD, "matrices": 64,
+                           "steps_include": "device reset copy + every matrix of this rank's shard"},
+                "rank0": res}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -369,13 +454,19 @@ def read_kernel_stats(lib):
     return stats
 
 
-def roofline_of(stats, prec, fp64_peak, peaks):
-    """Roofline of the dominant kernel of one step (largest summed device time)."""
+def roofline_of(stats, prec, fp64_peak, peaks, workload=None):
+    """Roofline of the dominant kernel of one step (largest summed device time).
+    `achieved` is its algorithmic flops summed over the step's launches divided by
+    their summed device time (CUDA events around each launch on its stream)."""
     top = max(stats.items(), key=lambda kv: kv[1][0])
     name, (ms, fl, cnt) = top
     total = sum(v[0] for v in stats.values())
+    tr = traffic_of(name, workload)
     base = {"kernel": name, "kernel_share_of_step": round(ms / total, 4) if total else None,
-            "avg_launch_ms": round(ms / max(cnt, 1), 5), "launches_per_step": int(cnt), "traffic": None}
+            "avg_launch_ms": round(ms / max(cnt, 1), 5), "launches_per_step": int(cnt),
+            "traffic": tr["bytes_per_launch"] if tr else None}
+    if tr:
+        base["traffic_capture"] = tr["capture"]
     if name == "gemm_tc":
         pairs = TC_PAIRS.get(prec, 1)
         ach = pairs * fl / (ms * 1e-3) / 1e12
@@ -404,36 +495,34 @@ def blockerr(x, y):
     return float(torch.linalg.norm(x - y) / torch.linalg.norm(y).clamp_min(1e-300))
 
 
-def run_modes(args, bta, lib, step, step_seq, W, ld_out, base_ms, dev, ref_inputs, base_phases):
+def _timed_steps(fn, steps, warmup, dev):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def run_modes(args, bta, lib, step, step_seq, W, ld_out, base_ms, dev, ref_inputs, base_phases,
+              peak_tf, workload):
     """Time the other precision modes on the same matrix; state each one's error
     against the main mode's result (per block, relative Frobenius) and its speedup."""
     import torch
     ref = [x.clone() for x in W]
     ref_ld = float(ld_out.item())
     res = {}
+    ms_steps, ms_warm = max(1, min(args.steps, args.mode_steps)), max(1, min(args.warmup, args.mode_warmup))
     for mode in [m for m in (args.modes or "").split(",") if m and m != args.precision]:
+        _log(f"mode {mode}")
         bta.set_precision(mode)
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            step()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / args.steps
-
-        def blockerr(x, y):
-            if x.numel() == 0:
-                return 0.0
-            if x.dim() == 3:
-                num = torch.linalg.norm((x - y).flatten(1), dim=1)
-                den = torch.linalg.norm(y.flatten(1), dim=1).clamp_min(1e-300)
-                return float((num / den).max())
-            return float(torch.linalg.norm(x - y) / torch.linalg.norm(y).clamp_min(1e-300))
-
+        ms = _timed_steps(step, ms_steps, ms_warm, dev)
         errs = {nm: blockerr(W[i], ref[i]) for i, nm in enumerate(["X_diag", "X_lower", "X_arrow", "X_tip"])}
         errs["solve"] = blockerr(W[4], ref[4])
         errs["logdet"] = abs(float(ld_out.item()) - ref_ld) / abs(ref_ld)
@@ -457,15 +546,17 @@ def run_modes(args, bta, lib, step, step_seq, W, ld_out, base_ms, dev, ref_input
         stats = read_kernel_stats(lib)
         lib.bta_timing_enable(0)
         peaks = measured_peaks()
-        res[mode] = {"phase_ms": phases,"ms_per_matrix": round(ms, 3), "speedup_vs_" + args.precision: round(base_ms / ms, 3),
+        res[mode] = {"phase_ms": phases, "ms_per_matrix": round(ms, 3), "steps": ms_steps, "warmup": ms_warm,
+                     "speedup_vs_" + args.precision: round(base_ms / ms, 3),
                      "max_block_rel_err_vs_" + args.precision: {k: float(f"{v:.3e}") for k, v in errs.items()},
                      "dtype": PREC_DTYPE[mode],
-                     "roofline": roofline_of(stats, mode, 1.0, peaks),
+                     "roofline": roofline_of(stats, mode, peak_tf, peaks, workload),
                      "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()}}
     # Partitioned form (the paper's P-way scheme on one device): factor + logdet + selinv.
     for spec in [x for x in (args.partitioned or "").split(",") if x]:
         prec, P = spec.split(":")
         P = int(P)
+        _log(f"partitioned {prec} P={P}")
         bta.set_precision(prec)
 
         def pstep():
@@ -473,17 +564,7 @@ def run_modes(args, bta, lib, step, step_seq, W, ld_out, base_ms, dev, ref_input
                 dst.copy_(src, non_blocking=True)
             bta.factor_selinv_partitioned(W[0], W[1], W[2], W[3], parts=P, lb=1.8, logdet_out=ld_out)
 
-        for _ in range(args.warmup):
-            pstep()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            pstep()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = _timed_steps(pstep, ms_steps, ms_warm, dev)
         errs = {nm: blockerr(W[i], ref[i]) for i, nm in enumerate(["X_diag", "X_lower", "X_arrow", "X_tip"])}
         errs["logdet"] = abs(float(ld_out.item()) - ref_ld) / abs(ref_ld)
         base_fls = base_phases["factor"] + base_phases["logdet"] + base_phases["selinv"]
@@ -508,7 +589,9 @@ def run_ours(args, w, rank, world, local_rank):
     lib = _lib.load()
     n, b, a = w["n"], w["b"], w["a"]
     bta.set_precision(args.precision)
+    wname = f"n{n}_b{b}_a{a}"
 
+    _log(f"generating {wname} (seed {rank_seed(rank)})")
     arrays = make_workload(w, seed=rank_seed(rank))
     d, l, ar, t, r = arrays
     P = [torch.from_numpy(x).to(dev) for x in (d, l, ar, t, r)]
@@ -538,12 +621,14 @@ def run_ours(args, w, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    _log(f"warmup x{args.warmup}")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
     if bta.get_info(dev) != 0:
         raise RuntimeError("non-positive pivot in the benchmark matrix")
 
+    _log(f"timed x{args.steps}")
     sampler = ClockSampler(local_rank)
     barrier()
     torch.cuda.synchronize(dev)
@@ -566,9 +651,10 @@ def run_ours(args, w, rank, world, local_rank):
     # End to end through the public API with host buffers (pinned): one call
     # (bta_factor_selinv_host) copies the pattern and right-hand sides in, runs
     # factor + logdet + solve + selinv, and copies X, x and log det back, the
-    # copies overlapped with the block sweeps.
+    # copies overlapped with the block sweeps. Timed over the same K steps.
     e2e = None
     if not args.no_e2e:
+        _log(f"e2e x{args.steps}")
         H = [torch.from_numpy(x).pin_memory() for x in (d, l, ar, t, r)]
         O = tuple([torch.empty(x.shape, dtype=torch.float64).pin_memory() for x in (d, l, ar, t, r)]
                   + [torch.empty((), dtype=torch.float64).pin_memory()])
@@ -579,9 +665,8 @@ def run_ours(args, w, rank, world, local_rank):
         e2e_step()
         torch.cuda.synchronize(dev)
         barrier()
-        k2 = max(1, min(args.steps, 2))
         e0.record()
-        for _ in range(k2):
+        for _ in range(args.steps):
             e2e_step()
         e1.record()
         torch.cuda.synchronize(dev)
@@ -590,23 +675,25 @@ def run_ours(args, w, rank, world, local_rank):
         h2d = sum(x.numel() * 8 for x in H)
         d2h = sum(x.numel() * 8 for x in O)
         # The host results against the device path's (W holds X after the timed steps).
-        torch.cuda.synchronize(dev)
         idx = sorted({0, n // 2, n - 1})
         sel = torch.tensor(idx)
         e2e_err = blockerr(O[0][sel], W[0][sel.to(dev)].cpu())
         if n > 1:
             sl = sel.clamp(max=n - 2)
             e2e_err = max(e2e_err, blockerr(O[1][sl], W[1][sl.to(dev)].cpu()))
-        e2e = {"value": round(ms2 / k2 / world, 3), "unit": "ms/matrix", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "max_block_rel_err_vs_device_path": float(f"{e2e_err:.3e}")}
+        e2e = {"value": round(ms2 / args.steps / world, 3), "unit": "ms/matrix", "steps": args.steps,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "max_block_rel_err_vs_device_path": float(f"{e2e_err:.3e}")}
         del H, O
 
     F = flops_factor(n, b, a) + flops_selinv(n, b, a)
     modes = {}
+    batched = None
     out = None
     if rank == 0:
         # Kernel-level measurement pass (after the timed steps): per-launch events
         # around every library kernel of one step, then the FP64 DMMA peak probe.
+        _log("phase split and per-kernel pass")
         stream = torch.cuda.current_stream(dev)
         # Phase split of one step (events between the C calls on the stream).
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -643,7 +730,8 @@ def run_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         peak_tf = pf.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
         if args.modes or args.partitioned:
-            modes = run_modes(args, bta, lib, step, step_seq, W, ld_out, ms_per_step, dev, P, phases)
+            modes = run_modes(args, bta, lib, step, step_seq, W, ld_out, ms_per_step, dev, P, phases,
+                              peak_tf, wname)
             bta.set_precision(args.precision)
 
         total_kernel_ms = sum(v[0] for v in stats.values())
@@ -658,7 +746,7 @@ def run_ours(args, w, rank, world, local_rank):
             "tflops_per_gpu": round(tflops, 4),
             "fp64_peak_tflops_measured": round(peak_tf, 4),
             "frac_of_fp64_peak": round(tflops / peak_tf, 4),
-            "roofline": roofline_of(stats, args.precision, peak_tf, peaks),
+            "roofline": roofline_of(stats, args.precision, peak_tf, peaks, wname),
             # the solve (a sequential chain of latency-bound triangular solves) against HBM
             "solve_roofline": {
                 "bound": "latency", "unit": "GB/s", "peak": peaks["hbm_gbs"],
@@ -667,6 +755,7 @@ def run_ours(args, w, rank, world, local_rank):
                               / peaks["hbm_gbs"], 4),
                 "traffic": None, "peak_source": peaks["source"]},
             "kernel_ms_per_step": {k: round(v[0], 3) for k, v in stats.items()},
+            "kernel_launches_per_step": {k: int(v[2]) for k, v in stats.items()},
             "kernel_total_ms_per_step": round(total_kernel_ms, 3),
             "phase_ms": phases,
             "gpu_launches": int(launches_per_step * args.steps),
@@ -675,10 +764,21 @@ def run_ours(args, w, rank, world, local_rank):
         }
         if clocks:
             out["clocks"] = clocks
+    # The main workload's device buffers are no longer needed.
+    del P, W
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_batch:
+        _log("batched form")
+        batched = batch_measure(max(1, min(args.steps, args.mode_steps)), max(1, min(args.warmup, args.mode_warmup)),
+                                dev, oracle_sample=args.batch_oracle_sample, quick_tune=True)
+        out["batched"] = dict(batched, workload=BATCH_WORKLOAD)
+    if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            per_full, desc, cores = cpu_oracle_sample(w, arrays, target_s=args.cpu_target_s)
+            _log("cpu baseline (oracle)")
+            per_full, desc, cores, _, _ = cpu_oracle_sample(w, arrays, target_s=args.cpu_target_s)
             out["cpu_baseline"] = {"value": round(per_full, 3), "unit": "ms/matrix", "cores": cores,
                                    "kind": "oracle", "sample": desc}
+        _log("done")
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
@@ -691,15 +791,20 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="n365_b1024_a8")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="n256_b2048_a16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     ap.add_argument("--precision", choices=["fp64", "ozaki", "bf16x3"], default="fp64")
     ap.add_argument("--modes", default="ozaki,bf16x3",
                     help="other precision modes timed on the same matrix ('' to skip)")
-    ap.add_argument("--partitioned", default="ozaki:4,ozaki:8,fp64:4",
-                    help="partitioned runs 'precision:P,...' timed on the same matrix ('' to skip)")
+    ap.add_argument("--partitioned", default="",
+                    help="partitioned runs 'precision:P,...' timed on the same matrix (e.g. ozaki:8)")
+    ap.add_argument("--mode-steps", type=int, default=3, help="timed steps per extra precision mode")
+    ap.add_argument("--mode-warmup", type=int, default=1, help="warm-up steps per extra precision mode")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form sub-record")
+    ap.add_argument("--batch-oracle-sample", type=int, default=4,
+                    help="matrices of the batched result checked against the oracle")
     ap.add_argument("--cpu-target-s", type=float, default=10.0)
     ap.add_argument("--ref-target-s", type=float, default=5.0)
     args = ap.parse_args()
@@ -707,17 +812,19 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload == BATCH_WORKLOAD:
-        return run_batch(args) if args.impl == "ours" else 0
-    w = WORKLOADS[args.workload]
+    if args.workload == BATCH_WORKLOAD and args.impl == "reference":
+        return 0
     if args.impl == "reference":
-        return run_reference(args, w, rank, world)
+        return run_reference(args, WORKLOADS[args.workload], rank, world)
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    rc = run_ours(args, w, rank, world, local_rank)
+    if args.workload == BATCH_WORKLOAD:
+        rc = run_batch(args, rank, world, local_rank)
+    else:
+        rc = run_ours(args, WORKLOADS[args.workload], rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
