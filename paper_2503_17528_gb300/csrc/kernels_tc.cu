@@ -7,28 +7,44 @@
 //    of op(A) (column of op(B)) gets a power-of-two scale 2^e with all entries
 //    below 2^(e-1); the scaled value is rounded to a 7*s-bit integer Y and cut
 //    into s balanced base-128 digits d_1..d_s (|d_1| <= 65, |d_p| <= 64), stored
-//    as BF16 values d_p * 2^-7p (exact). Products of digit slices p, q are
-//    grouped by d = p + q: groups d = 2..6 each accumulate in their own FP32 TMEM
-//    accumulator over k-units of at most 512, where every partial sum is an
-//    integer multiple of 2^-7d below 2^24 of them (so it is exact whatever the
-//    accumulator's rounding mode); groups d >= 7 share one accumulator that sits
-//    2^-35 below the leading group. Pairs with d > s + 1 are dropped (triangular
-//    truncation). Each k-unit's groups are combined into one int64 fixed-point
-//    value (quantum 2^-49 of the scales) and summed with integer atomics, which
-//    makes the k split exact and the result independent of summation order; a
-//    finalize kernel converts to FP64 and applies the scales, alpha and beta.
+//    as BF16 values d_p * 2^-7p (exact). Products of digit slices p, q (0-based)
+//    are grouped by g = p + q, and pairs with g > s - 1 are dropped (triangular
+//    truncation). Each group accumulates in its own FP32 TMEM accumulator over
+//    k-units of at most 512: a group holds at most s pairs of digit products
+//    |d d'| <= 65 * 64, so every partial sum is an integer multiple of 2^-7(g+2)
+//    below 2^24 of them and exact whatever the accumulator's rounding. Each
+//    k-unit's groups become one int64 fixed-point value (quantum 2^-49 of the
+//    scales; the g = 6 group is rounded to it), and the units of a tile are
+//    summed in integers: exact and independent of order. The FP64 output is then
+//    assembled from the integer with integer operations (the scales are powers of
+//    two), which keeps the epilogue off this part's narrow FP64 pipe.
 //  * X3 (mixed precision): x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the
-//    products hi*hi + hi*lo + lo*hi accumulate in one FP32 accumulator.
+//    products hi*hi (group 0) and hi*lo + lo*hi (group 1) accumulate in FP32 and
+//    are added at the end.
 //
-// Tile: 128 x 64 outputs per CTA and one k-unit (OZ: <= 512; X3: all of k),
-// k-blocks of 32 BF16 (64-byte rows, 64-byte swizzle), every slice of A and B
-// for a k-block in one pipeline stage. Warp 0 issues TMA loads, warp 1 issues
-// tcgen05.mma, all four warps run the epilogue from TMEM. Every wait is bounded: on a timeout the kernel records an error,
-// drains what it issued, frees its TMEM and returns.
+// Slice p of op(A) against slices q0..q0+c-1 of op(B) is ONE tcgen05.mma with
+// N = 64c (c <= 4): the B slices sit one after another in shared memory, and the
+// accumulators of groups p+q0 .. p+q0+c-1 sit one after another in TMEM (group g
+// at column 64g). Seven digit slices take 10 MMAs per 16-deep k step instead of
+// 28, each reading its A slice once for up to 256 output columns.
+//
+// Tile: 128 x 64 outputs; k-blocks of 32 BF16 (64-byte rows, 64-byte swizzle),
+// every slice of A and B for a k-block in one pipeline stage, loaded by two 3-D
+// TMA copies (slices as the third dimension). Persistent, warp-specialized CTAs
+// (one per SM): warp 8 issues TMA, warp 9 issues tcgen05.mma, warps 0-7 drain the
+// accumulators (warp w reads TMEM lanes 32(w%4).. and columns 32(w/4)..). A work
+// item is one output tile and a range of its k-units; when every tile holds all
+// of its units the result is written directly, otherwise the items add int64
+// partial tiles with atomics and a finalize kernel writes C. Every wait is
+// bounded: on a timeout the kernel records an error, stops issuing, drains what
+// it issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
 
 #include "bta_internal.cuh"
 #include "kernels_tc.cuh"
@@ -38,10 +54,11 @@ namespace bta {
 namespace tc {
 
 constexpr int BM = 128, BN = 64, BK = 32;
-constexpr int kUnitK = 512;     // k per unit in OZ mode (exactness bound of the d = 6 group)
-constexpr int kOzGroups = 6;    // d = 2..6 exact, d >= 7 shared
+constexpr int kUnitK = 512;     // k per unit in OZ mode (exactness bound of the digit groups)
 constexpr int kFixShift = 49;   // int64 fixed point: value = T * 2^-49 * scales
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr uint32_t kSpinLimit = 1u << 22;  // polls of try_wait (each suspends ~us) before giving up
 constexpr int kMaxStages = 4;
 
@@ -59,6 +76,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -81,17 +102,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
+// 3-D tiled TMA load (x = k, y = row, z = slice plane) completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major tile, rows of 64 bytes, 64-byte
-// swizzle, 8-row groups 512 bytes apart (descriptor version 1).
+// swizzle, 8-row groups 512 bytes apart (descriptor version 1). Rows continue
+// across slice boundaries (each slice is a whole number of 8-row groups), so one
+// descriptor can span several consecutive slices.
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -123,13 +147,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
       : "r"(taddr));
 }
 
@@ -149,24 +177,118 @@ __device__ __forceinline__ double* c_base(const COut& c, int zl) {
   return c.C + (int64_t)(z % c.nb1) * c.s1 + (int64_t)(z / c.nb1) * c.s2;
 }
 
+// Exact FP32 -> FP64 with integer operations (normal numbers and zeros; the
+// rare rest through the conversion instruction).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (u & 0x7fffffffu) ? (double)f : __longlong_as_double((long long)(u >> 31) << 63);
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(e + 896u) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// v * 2^(s - 49), rounded to nearest even, for the int64 accumulator v, with
+// integer operations; s is the sum of the power-of-two scales' exponents.
+// Results outside the normal range take the FP64 path.
+__device__ __forceinline__ double fix_to_f64(long long v, int s) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 1ull : 0ull;
+  unsigned long long m = sign ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int top = 63 - __clzll((long long)m);  // index of the leading one
+  if (top > 52) {
+    const int sh = top - 52;
+    const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m >>= sh;
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++top;
+    }
+  } else {
+    m <<= (52 - top);
+  }
+  const int biased = top - kFixShift + s + 1023;
+  if (biased < 1 || biased > 2046) return ldexp((double)v, s - kFixShift);
+  return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)biased << 52) |
+                                          (m & 0xfffffffffffffull)));
+}
+
+// Exponent of a power of two held as a double; returns false for anything else
+// (NaN rows, zero scales, non-powers).
+__device__ __forceinline__ bool pow2_exponent(double x, int& e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if ((b & 0xfffffffffffffull) || be == 0 || be == 2047 || (b >> 63)) return false;
+  e = be - 1023;
+  return true;
+}
+
 struct TcArgs {
-  int M, N;          // logical output size
-  int Kc;            // padded k extent of the slices (multiple of BK)
-  int unitk;         // k per work unit (multiple of BK)
-  int nunits;        // units per tile (grid = tiles x units x batch)
-  long long* T;      // OZ: [nb][Mpad][Npad] int64 accumulators (zeroed by the host)
-  int s;             // slices per operand
-  int mode;          // TC_OZ or TC_X3
-  int Mpad, Npad;    // padded rows of the A / B slice planes
+  int M, N;           // logical output size
+  int Kc;             // padded k extent of the slices (multiple of BK)
+  int unitk;          // k per unit (multiple of BK)
+  int nunits;         // units per tile
+  int ups;            // units per work item
+  int chunks;         // work items per tile (chunks == 1: direct write)
+  int tilesN;         // tile columns
+  int tiles_z;        // computed tiles per batch entry (lower tiles only if lowerC)
+  long long items;    // nb * tiles_z * chunks
+  long long* T;       // chunks > 1: [nb][Mpad][Npad] int64 accumulators (zeroed before)
+  int s;              // slices per operand
+  int gmax;           // largest group index kept (OZ: s - 1; X3: 1)
+  int mode;           // TC_OZ or TC_X3
+  int Mpad, Npad;     // padded rows of the A / B slice planes
   int nstages;
-  int triA, triB;    // structure of op(A), op(B) (TRI_*), global k coordinates
+  int triA, triB;     // structure of op(A), op(B) (TRI_*), global k coordinates
   int lowerC;
-  int nb;            // batch count
-  const double* sa;  // [nb][Mpad] row scales of A
-  const double* sb;  // [nb][Npad] column scales of B
+  const double* sa;   // [nb][Mpad] row scales of A
+  const double* sb;   // [nb][Npad] column scales of B
   COut co;
   double alpha, beta;
 };
+
+// Output tiles of a row of tiles (all, or those touching the lower triangle).
+__device__ __forceinline__ int tiles_in_row(const TcArgs& g, int tm) {
+  if (!g.lowerC) return g.tilesN;
+  const int c = (tm * BM + BM - 1) / BN + 1;
+  return c < g.tilesN ? c : g.tilesN;
+}
+
+// Work item -> batch entry z, tile (tm, tn), units [u0, u1).
+__device__ __forceinline__ void decode_item(const TcArgs& g, long long item, int& z, int& tm, int& tn,
+                                            int& u0, int& u1) {
+  const int c = (int)(item % g.chunks);
+  item /= g.chunks;
+  int t = (int)(item % g.tiles_z);
+  z = (int)(item / g.tiles_z);
+  if (!g.lowerC) {
+    tm = t / g.tilesN;
+    tn = t % g.tilesN;
+  } else {
+    tm = 0;
+    for (int w = tiles_in_row(g, 0); t >= w; w = tiles_in_row(g, ++tm)) t -= w;
+    tn = t;
+  }
+  u0 = c * g.ups;
+  u1 = min(g.nunits, u0 + g.ups);
+}
+
+// k-block range [kb, kb + nk*BK) of unit u of tile (tm, tn); structural zeros of
+// triangular operands are skipped.
+__device__ __forceinline__ int unit_kblocks(const TcArgs& g, int tm, int tn, int u, int& kb) {
+  const int m0 = tm * BM, n0 = tn * BN;
+  int gb = 0, ge = g.Kc;
+  if (g.triA == TRI_LOWER) ge = min(ge, m0 + BM);
+  if (g.triA == TRI_UPPER) gb = max(gb, m0);
+  if (g.triB == TRI_LOWER) gb = max(gb, n0);
+  if (g.triB == TRI_UPPER) ge = min(ge, n0 + BN);
+  gb = gb / BK * BK;
+  kb = max(gb, u * g.unitk);
+  const int ke = min(ge, (u + 1) * g.unitk);
+  return ke > kb ? (ke - kb + BK - 1) / BK : 0;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -174,50 +296,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
-  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t tfull_bar;   // accumulators ready (MMA commit)
+  __shared__ __align__(8) uint64_t tempty_bar;  // accumulators drained (kEpiWarps arrivals)
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  // Work unit -> (batch z, tile (tm, tn), k-unit u).
-  const int tilesM = (g.M + BM - 1) / BM, tilesN = (g.N + BN - 1) / BN;
-  long long bid = blockIdx.x;
-  const int u = (int)(bid % g.nunits);
-  bid /= g.nunits;
-  const int tn = (int)(bid % tilesN);
-  bid /= tilesN;
-  const int tm = (int)(bid % tilesM);
-  const int z = (int)(bid / tilesM);
-  const int m0 = tm * BM, n0 = tn * BN;
-  if (g.lowerC && n0 > m0 + BM - 1) return;  // tile entirely above the diagonal
-
-  // k-block range of this unit (structural zeros of triangular operands skipped).
-  int kb, ke;
-  {
-    int gb = 0, ge = g.Kc;
-    if (g.triA == TRI_LOWER) ge = min(ge, m0 + BM);
-    if (g.triA == TRI_UPPER) gb = max(gb, m0);
-    if (g.triB == TRI_LOWER) gb = max(gb, n0);
-    if (g.triB == TRI_UPPER) ge = min(ge, n0 + BN);
-    gb = gb / BK * BK;
-    kb = max(gb, u * g.unitk);
-    ke = min(ge, (u + 1) * g.unitk);
-  }
-  const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
-  if (nk == 0 && (g.mode == TC_OZ || u > 0)) return;  // nothing to add (X3 unit 0 still writes beta*C)
-
-  const int S = g.s;
+  const int S = g.s, NS = g.nstages;
   const uint32_t a_bytes = BM * BK * 2, b_bytes = BN * BK * 2;
   const uint32_t stage_bytes = (uint32_t)S * (a_bytes + b_bytes);
-  const int NS = g.nstages;
 
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
-    mbar_init(&done_bar, 1);
+    mbar_init(&tfull_bar, 1);
+    mbar_init(&tempty_bar, kEpiWarps);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -231,128 +328,195 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const int ngroups = g.mode == TC_OZ ? min(kOzGroups, S) : 1;
 
-  if (nk > 0) {
-    if (warp == 0 && lane == 0) {
-      // TMA producer.
-      int issued = 0;
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      // TMA producer: every k-block of every unit of this CTA's items, in order.
+      long long it = 0;
       bool ok = true;
-      for (int it = 0; it < nk && ok; ++it) {
-        const int st = it % NS;
-        if (it >= NS) ok = mbar_wait(&empty_bar[st], ((it / NS) - 1) & 1);
-        if (!ok) break;
-        mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
-        uint8_t* sbase = smem + (size_t)st * stage_bytes;
-        const int kx = kb + it * BK;
-        for (int p = 0; p < S; ++p)
-          tma_load_2d(sbase + p * a_bytes, &tmA, &full_bar[st], kx, (z * S + p) * g.Mpad + m0);
-        for (int q = 0; q < S; ++q)
-          tma_load_2d(sbase + S * a_bytes + q * b_bytes, &tmB, &full_bar[st], kx,
-                      (z * S + q) * g.Npad + n0);
-        ++issued;
+      for (long long item = blockIdx.x; item < g.items && ok; item += gridDim.x) {
+        int z, tm, tn, u0, u1;
+        decode_item(g, item, z, tm, tn, u0, u1);
+        for (int u = u0; u < u1 && ok; ++u) {
+          int kb;
+          const int nk = unit_kblocks(g, tm, tn, u, kb);
+          for (int kk = 0; kk < nk; ++kk, ++it) {
+            const int st = (int)(it % NS);
+            if (it >= NS && !mbar_wait(&empty_bar[st], (uint32_t)((it / NS) - 1) & 1u)) ok = false;
+            if (!ok || s_abort) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
+            uint8_t* sbase = smem + (size_t)st * stage_bytes;
+            const int kx = kb + kk * BK;
+            tma_load_3d(sbase, &tmA, &full_bar[st], kx, tm * BM, z * S);
+            tma_load_3d(sbase + S * a_bytes, &tmB, &full_bar[st], kx, tn * BN, z * S);
+          }
+        }
       }
       if (!ok) {
-        // Drain the loads already in flight before leaving.
-        for (int it = max(0, issued - NS); it < issued; ++it) mbar_wait(&full_bar[it % NS], (it / NS) & 1);
+        s_abort = 1;
+        // Drain the loads still in flight (at most NS stages) before leaving.
+        for (long long j = it > NS ? it - NS : 0; j < it; ++j) mbar_wait(&full_bar[j % NS], (uint32_t)(j / NS) & 1u);
       }
-    } else if (warp == 1 && lane == 0) {
-      // MMA issuer.
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);  // 128 x 64
-      uint32_t started = 0;
-      for (int it = 0; it < nk; ++it) {
-        const int st = it % NS;
-        if (!mbar_wait(&full_bar[st], (it / NS) & 1)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sbase = smem_u32(smem + (size_t)st * stage_bytes);
-        for (int p = 0; p < S; ++p) {
-          for (int q = 0; q < S; ++q) {
-            int grp;
-            if (g.mode == TC_OZ) {
-              if (p + q > S - 1) continue;  // (p+1) + (q+1) > S + 1
-              grp = min(p + q, kOzGroups - 1);
-            } else {
-              if (p + q > 1) continue;      // hi*hi, hi*lo, lo*hi
-              grp = 0;
-            }
-            const uint32_t a_addr = sbase + p * a_bytes;
-            const uint32_t b_addr = sbase + S * a_bytes + q * b_bytes;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint32_t acc = (started >> grp) & 1u;
-              umma_bf16(tmem + grp * BN, sdesc_sw64(a_addr + kk * 32), sdesc_sw64(b_addr + kk * 32),
-                        idesc, acc);
-              started |= 1u << grp;
-            }
-          }
-        }
-        umma_commit(&empty_bar[st]);
-      }
-      umma_commit(&done_bar);
     }
-    // Epilogue: every warp reads its 32 TMEM lanes (rows).
-    __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0));
-    __syncwarp();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int row = m0 + warp * 32 + lane;
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-      if (g.mode == TC_OZ) {
-        // Exact groups -> integers, all groups -> one int64 in units of 2^-49.
-        long long* Tz = g.T + ((int64_t)z * g.Mpad + row) * g.Npad;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          long long acc[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = 0;
-#pragma unroll
-          for (int gi = 0; gi < kOzGroups; ++gi) {
-            if (gi >= ngroups) break;  // warp-uniform
-            uint32_t r[16];
-            tmem_ld16(lane_base + gi * BN + c0, r);
-            tmem_wait_ld();
-            // group gi holds sum d d' 2^-7(gi+2): exact groups -> integers, scaled to 2^-49 units;
-            // the shared group is rounded to the 2^-49 quantum
-            const float up = __int_as_float((127 + (gi < kOzGroups - 1 ? 7 * (gi + 2) : kFixShift)) << 23);
-            const int sh = gi < kOzGroups - 1 ? kFixShift - 7 * (gi + 2) : 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] += __float2ll_rn(__uint_as_float(r[j]) * up) << sh;
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // MMA issuer.
+      long long it = 0, tuse = 0;
+      bool ok = true;
+      for (long long item = blockIdx.x; item < g.items && ok; item += gridDim.x) {
+        int z, tm, tn, u0, u1;
+        decode_item(g, item, z, tm, tn, u0, u1);
+        for (int u = u0; u < u1 && ok; ++u) {
+          int kb;
+          const int nk = unit_kblocks(g, tm, tn, u, kb);
+          if (nk == 0) continue;
+          // The epilogue must have drained the previous unit's accumulators.
+          if (tuse > 0 && !mbar_wait(&tempty_bar, (uint32_t)(tuse - 1) & 1u)) ok = false;
+          if (!ok || s_abort) {
+            ok = false;
+            break;
           }
-          if (row < g.M) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (acc[j]) atomicAdd((unsigned long long*)(Tz + n0 + c0 + j), (unsigned long long)acc[j]);
-          }
-        }
-      } else {
-        double* Cz = c_base(g.co, z);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(lane_base + c0, r);
-          tmem_wait_ld();
-          if (row < g.M) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int col = n0 + c0 + j;
-              if (col >= g.N) break;
-              double* p = Cz + (int64_t)row * g.co.ldc + col;
-              double out = g.alpha * (double)__uint_as_float(r[j]);
-              if (g.beta != 0.0) out += g.beta * *p;
-              *p = out;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int kk = 0; kk < nk; ++kk, ++it) {
+            const int st = (int)(it % NS);
+            if (!mbar_wait(&full_bar[st], (uint32_t)(it / NS) & 1u) || s_abort) {
+              ok = false;
+              break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sbase = smem_u32(smem + (size_t)st * stage_bytes);
+#pragma unroll
+            for (int k16 = 0; k16 < BK / 16; ++k16) {
+              for (int p = 0; p < S; ++p) {
+                const int m = min(S, g.gmax + 1 - p);  // B slices q = 0 .. m-1 meet slice p
+                const uint64_t adesc = sdesc_sw64(sbase + p * a_bytes + k16 * 32);
+                for (int q0 = 0; q0 < m; q0 += 4) {
+                  const int c = min(4, m - q0);
+                  const uint32_t acc = (kk > 0 || k16 > 0 || p > 0) ? 1u : 0u;
+                  umma_bf16(tmem + (uint32_t)((p + q0) * BN),
+                            adesc, sdesc_sw64(sbase + S * a_bytes + q0 * b_bytes + k16 * 32),
+                            idesc_bf16_f32(BM, c * BN), acc);
+                }
+              }
+            }
+            umma_commit(&empty_bar[st]);
           }
+          if (!ok) break;
+          umma_commit(&tfull_bar);
+          ++tuse;
         }
+      }
+      if (!ok) {
+        // Every MMA this CTA issued completes before its TMEM is freed: one more
+        // commit, and a wait for the phase it completes.
+        s_abort = 1;
+        umma_commit(&tfull_bar);
+        mbar_wait(&tfull_bar, (uint32_t)tuse & 1u);
       }
     }
   } else {
-    // X3 with an empty k-range: C = beta * C on this tile.
-    const int row = m0 + warp * 32 + lane;
-    double* Cz = c_base(g.co, z);
-    if (row < g.M)
-      for (int c = 0; c < BN && n0 + c < g.N; ++c) {
-        double* p = Cz + (int64_t)row * g.co.ldc + n0 + c;
-        *p = g.beta != 0.0 ? g.beta * *p : 0.0;
+    // Epilogue warps: rows m0 + 32 (warp % 4) + lane, columns n0 + 32 (warp / 4) + j.
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    long long tuse = 0;
+    bool ok = true;
+    for (long long item = blockIdx.x; item < g.items && ok; item += gridDim.x) {
+      int z, tm, tn, u0, u1;
+      decode_item(g, item, z, tm, tn, u0, u1);
+      const int row = tm * BM + quarter * 32 + lane;
+      const int col0 = tn * BN + half * 32;
+      long long acc[32];
+      float accf[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        acc[j] = 0;
+        accf[j] = 0.f;
       }
+      for (int u = u0; u < u1; ++u) {
+        int kb;
+        if (unit_kblocks(g, tm, tn, u, kb) == 0) continue;
+        if (!mbar_wait(&tfull_bar, (uint32_t)tuse & 1u) || s_abort) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (g.mode == TC_OZ) {
+          for (int gi = 0; gi <= g.gmax; ++gi) {
+            uint32_t r[32];
+            tmem_ld32(lane_base + (uint32_t)(gi * BN), r);
+            tmem_wait_ld();
+            if (gi <= 5) {
+              // exact group: v 2^(7(gi+2)) is an integer below 2^24
+              const float up = __int_as_float((127 + 7 * (gi + 2)) << 23);
+              const int sh = kFixShift - 7 * (gi + 2);
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                acc[j] += (long long)__float2int_rn(__uint_as_float(r[j]) * up) << sh;
+            } else {
+              // the g = 6 group: rounded to the 2^-49 quantum
+              const float up = __int_as_float((127 + kFixShift) << 23);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j]) * up);
+            }
+          }
+        } else {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(lane_base, r0);
+          tmem_ld32(lane_base + (uint32_t)BN, r1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) accf[j] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty_bar);
+        ++tuse;
+      }
+      if (!ok) break;
+      if (row >= g.M) continue;
+      if (g.chunks > 1) {
+        long long* Tz = g.T + ((int64_t)z * g.Mpad + row) * g.Npad + col0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (acc[j]) atomicAdd((unsigned long long*)(Tz + j), (unsigned long long)acc[j]);
+        continue;
+      }
+      // Direct write: C = alpha * result + beta * C on the defined elements.
+      double* Cz = c_base(g.co, z) + (int64_t)row * g.co.ldc;
+      int ea = 0, eb = 0;
+      const bool fastA = g.mode == TC_OZ ? pow2_exponent(g.sa[(int64_t)z * g.Mpad + row], ea) : true;
+      const bool neg = g.alpha == -1.0;
+      const bool unit_alpha = g.alpha == 1.0 || neg;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = col0 + j;
+        if (col >= g.N) break;
+        double v;
+        if (g.mode == TC_OZ) {
+          const double sbj = g.sb[(int64_t)z * g.Npad + col];
+          if (fastA && pow2_exponent(sbj, eb)) {
+            v = fix_to_f64(acc[j], ea + eb);
+          } else {
+            v = ((double)acc[j] * (1.0 / (double)(1ll << kFixShift))) * g.sa[(int64_t)z * g.Mpad + row] * sbj;
+          }
+        } else {
+          v = f32_to_f64(accf[j]);
+        }
+        if (unit_alpha) {
+          if (neg) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+        } else {
+          v *= g.alpha;
+        }
+        double* p = Cz + col;
+        if (g.beta == 1.0) v += *p;
+        else if (g.beta != 0.0) v += g.beta * *p;
+        *p = v;
+      }
+    }
+    if (!ok) s_abort = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -548,7 +712,9 @@ __global__ void __launch_bounds__(256) split_digits_kernel(SplitOp sa_op, SplitO
   }
 }
 
-// C = alpha * T 2^-49 sa_i sb_j + beta * C on the elements the GEMM computed.
+
+// C = alpha * T 2^-49 sa_i sb_j + beta * C for tiles split over several work
+// items (their int64 partial tiles summed in T), on the elements the GEMM defines.
 __global__ void __launch_bounds__(256) tc_finalize_kernel(const long long* T, int M, int N, int Mpad,
                                                           int Npad, const double* sa,
                                                           const double* sb, COut co, double alpha,
@@ -558,11 +724,17 @@ __global__ void __launch_bounds__(256) tc_finalize_kernel(const long long* T, in
   if (e >= (int64_t)M * N) return;
   const int i = (int)(e / N), j = (int)(e % N);
   if (lowerC && (j / BN) * BN > (i / BM) * BM + BM - 1) return;
-  const double v = (double)T[((int64_t)zl * Mpad + i) * Npad + j];
-  const double q = 1.0 / (double)(1ll << kFixShift);  // 2^-49, exact
-  double out = (v * q) * (alpha * sa[(int64_t)zl * Mpad + i]) * sb[(int64_t)zl * Npad + j];
+  const long long t = T[((int64_t)zl * Mpad + i) * Npad + j];
+  const double si = sa[(int64_t)zl * Mpad + i], sj = sb[(int64_t)zl * Npad + j];
+  int ea, eb;
+  double out;
+  if (pow2_exponent(si, ea) && pow2_exponent(sj, eb)) out = fix_to_f64(t, ea + eb);
+  else out = ((double)t * (1.0 / (double)(1ll << kFixShift))) * si * sj;
+  if (alpha == -1.0) out = __longlong_as_double(__double_as_longlong(out) ^ (long long)0x8000000000000000ull);
+  else if (alpha != 1.0) out *= alpha;
   double* p = c_base(co, zl) + (int64_t)i * co.ldc + j;
-  if (beta != 0.0) out += beta * *p;
+  if (beta == 1.0) out += *p;
+  else if (beta != 0.0) out += beta * *p;
   *p = out;
 }
 
@@ -579,26 +751,33 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static std::atomic<EncodeTiledFn> fn{nullptr};
+  EncodeTiledFn f = fn.load();
+  if (!f) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
+        q == cudaDriverEntryPointSuccess) {
+      f = (EncodeTiledFn)p;
+      fn.store(f);
+    }
   }
-  return fn;
+  return f;
 }
 
-static bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t kp, int box_rows) {
+// 3-D map over `planes` slice planes of `rows` x kp BF16 (row-major, kp
+// contiguous); one box is BK x box_rows x slices (every slice of one row block
+// for one k-block).
+static bool make_map(CUtensorMap* m, void* base, uint64_t planes, uint64_t rows, uint64_t kp,
+                     int box_rows, int slices) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  const cuuint64_t dims[2] = {kp, rows};
-  const cuuint64_t strides[1] = {kp * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+  const cuuint64_t dims[3] = {kp, rows, planes};
+  const cuuint64_t strides[2] = {kp * 2, rows * kp * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)slices};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -615,7 +794,7 @@ static size_t tc_chunk_bytes(int mode, int M, int N, int K, int nb) {
   b += rup((Mp + Np) * Kp * s * 2 * nb, 256);  // slices
   b += rup((Mp + Np) * 8 * nb, 256);           // scales
   b += rup((Mp + Np) * 8 * nb, 256);           // row maxima
-  if (mode == TC_OZ) b += rup(Mp * Np * 8 * nb, 256);  // int64 accumulators
+  if (mode == TC_OZ) b += rup(Mp * Np * 8 * nb, 256);  // int64 accumulators (split tiles)
   return b;
 }
 
@@ -655,7 +834,9 @@ static void fill_op(SplitOp* op, const Part* parts, int np, int nb1, int zbase, 
   }
 }
 
-static PerDevice g_tc_dyn_limit;
+// Dynamic shared memory limit of the GEMM kernel (set on the kernel) and the SM
+// count, per device; -1 if a query failed.
+static PerDevice g_tc_dyn_limit, g_tc_sms;
 
 cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (g.nterms < 1 || g.nterms > kMaxTerms) return cudaErrorInvalidValue;
@@ -701,8 +882,6 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
   if (chunk_nb > total) chunk_nb = total;
   while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) --chunk_nb;
   if (tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
-  // Dynamic shared memory: the opt-in limit less the kernel's static shared
-  // memory, raised on the kernel once per device (-1: the query failed).
   const long long dyn_limit = per_device(g_tc_dyn_limit, []() -> long long {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa;
@@ -716,7 +895,14 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
       return -1;
     return lim;
   });
-  if (dyn_limit < 0) return cudaErrorInvalidConfiguration;
+  const long long sms = per_device(g_tc_sms, []() -> long long {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      return -1;
+    return n;
+  });
+  if (dyn_limit < 0 || sms < 0) return cudaErrorInvalidConfiguration;
   const uint32_t stage_bytes = (uint32_t)S * (BM + BN) * BK * 2;
   int nstages = (int)((dyn_limit - 1024) / stage_bytes);
   if (nstages > kMaxStages) nstages = kMaxStages;
@@ -725,9 +911,25 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
   const int unitk = mode == TC_OZ ? kUnitK : Kp;
   const int nunits = (Kp + unitk - 1) / unitk;
   const GemmTerm& t0 = g.t[0];
+  // Output tiles per batch entry (only those touching the lower triangle for lowerC).
+  const int tilesM = Mp / BM, tilesN = Np / BN;
+  long long tiles_z = 0;
+  for (int tm = 0; tm < tilesM; ++tm) {
+    const int c = g.lowerC ? std::min(tilesN, (tm * BM + BM - 1) / BN + 1) : tilesN;
+    tiles_z += c;
+  }
 
   for (int c0 = 0; c0 < total; c0 += chunk_nb) {
     const int nb = total - c0 < chunk_nb ? total - c0 : chunk_nb;
+    // Work items: whole tiles when they fill every SM at least once; otherwise
+    // each tile's units are split over `chunks` items that add int64 partials.
+    const long long tiles = tiles_z * nb;
+    int chunks = 1;
+    if (nunits > 1 && tiles < sms) {
+      chunks = (int)std::min<long long>(nunits, (2 * sms + tiles - 1) / tiles);
+    }
+    const int ups = (nunits + chunks - 1) / chunks;
+    chunks = (nunits + ups - 1) / ups;
     char* w = (char*)ws;
     __nv_bfloat16* As = (__nv_bfloat16*)w;
     __nv_bfloat16* Bs = As + (int64_t)nb * S * Mp * Kp;
@@ -752,24 +954,25 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
         split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, 2 * nb), 256, 0, s>>>(opA, opB, rmA, rmB);
       }
       split_digits_kernel<<<dim3(Kp / 32, bands, 2 * nb), 256, 0, s>>>(
-          opA, opB, rmA, rmB, mode == TC_OZ ? Tacc : nullptr, Np);
+          opA, opB, rmA, rmB, (mode == TC_OZ && chunks > 1) ? Tacc : nullptr, Np);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     CUtensorMap mA, mB;
-    if (!make_map(&mA, As, (uint64_t)nb * S * Mp, (uint64_t)Kp, BM) ||
-        !make_map(&mB, Bs, (uint64_t)nb * S * Np, (uint64_t)Kp, BN))
+    if (!make_map(&mA, As, (uint64_t)nb * S, (uint64_t)Mp, (uint64_t)Kp, BM, S) ||
+        !make_map(&mB, Bs, (uint64_t)nb * S, (uint64_t)Np, (uint64_t)Kp, BN, S))
       return cudaErrorInvalidValue;
     TcArgs a{};
-    a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.T = Tacc;
-    a.s = S; a.mode = mode; a.Mpad = Mp; a.Npad = Np;
-    a.nstages = nstages; a.lowerC = g.lowerC; a.nb = nb;
+    a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.ups = ups; a.chunks = chunks;
+    a.tilesN = tilesN; a.tiles_z = (int)tiles_z; a.items = tiles * chunks;
+    a.T = Tacc; a.s = S; a.gmax = mode == TC_OZ ? S - 1 : 1; a.mode = mode;
+    a.Mpad = Mp; a.Npad = Np; a.nstages = nstages; a.lowerC = g.lowerC;
     a.triA = g.nterms == 1 ? t0.triA : TRI_NONE;
     a.triB = g.nterms == 1 ? t0.triB : TRI_NONE;
     a.sa = sa; a.sb = sb;
     a.co = COut{g.C, g.ldc, g.sC1, g.sC2, g.nb1, c0};
     a.alpha = t0.alpha; a.beta = g.beta;
-    const long long grid = (long long)(Mp / BM) * (Np / BN) * nunits * nb;
+    const long long grid = std::min<long long>(a.items, sms);
     {
       // algorithmic flops of this chunk's nb batch entries
       const double fl = timing_on() ? gemm_alg_flops(g) / total * nb : 0.0;
@@ -778,7 +981,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
-    if (mode == TC_OZ) {
+    if (mode == TC_OZ && chunks > 1) {
       const int64_t elems = (int64_t)M * N;
       TimedLaunch tl(K_TC_FINAL, 0.0, s);
       tc_finalize_kernel<<<dim3((unsigned)((elems + 255) / 256), nb), 256, 0, s>>>(
