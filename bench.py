@@ -46,8 +46,9 @@ WORKLOADS = {
     "n365_b1024_a8": dict(n=365, b=1024, a=8, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
     "n16_b32_a4": dict(n=16, b=32, a=4, shift=gen.SHIFT_PLUS_ONE, shift_name="1 + row sum"),
     "n256_b2048_a16": dict(n=256, b=2048, a=16, shift=gen.SHIFT_1_001, shift_name="1.001 x row sum"),
-    # small case with the same block shapes, for profiler captures (a few GB on the device)
+    # small cases with the same block shapes, for profiler captures (under 1 GB on the device)
     "n48_b1024_a8": dict(n=48, b=1024, a=8, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
+    "n8_b2048_a16": dict(n=8, b=2048, a=16, shift=gen.SHIFT_1_001, shift_name="1.001 x row sum"),
 }
 NRHS = 4
 BATCH_WORKLOAD = "batch64_n20-200_b128-512_a2-8"

@@ -93,9 +93,11 @@ int bta_selinv(int64_t n, int64_t b, int64_t a, double* diag, double* lower,
  * standard use of a Cholesky factor.
  *   y_i = L_ii^{-1}(r_i - L_{i,i-1} y_{i-1}),  y_n = L_nn^{-1}(r_n - sum_i L_{n,i} y_i)
  *   x_n = L_nn^{-T} y_n,  x_i = L_ii^{-T}(y_i - L_{i+1,i}^T x_{i+1} - L_{n,i}^T x_n)
- * rhs: [N][nrhs] row-major device buffer, 1 <= nrhs <= 64. Both sweeps use the
- * inverses of the 32 x 32 diagonal tiles of every L_ii, formed first in the
- * workspace (n * ceil(b/32) * 1024 doubles, besides the arrow partial sums).
+ * rhs: [N][nrhs] row-major device buffer, 1 <= nrhs <= 64. Inside a block the
+ * triangular solve is blocked by diagonal sub-blocks of order ds = min(b, 256),
+ * whose inverses are formed first in the workspace (n * ceil(b/ds) * ds^2
+ * doubles, besides the arrow partial sums and one block of staging): each block
+ * step is then ceil(b/ds) dependent pairs of matrix-vector products.
  */
 int bta_solve(int64_t n, int64_t b, int64_t a, const double* diag,
               const double* lower, const double* arrow, const double* tip,

@@ -42,7 +42,7 @@ struct SelinvWs { double *Linv, *G, *H, *LtInv; void* tc; size_t tc_bytes; };
 
 extern int g_prec;
 size_t tc_bytes_for(int64_t b, int64_t a, int64_t batch, int prec);
-struct SolveWs { double* partial; double* dinv; };
+struct SolveWs { double* partial; double* dinv; double* tmp; };
 struct LogdetWs { double* partial; };
 
 size_t factor_ws(int64_t n, int64_t b, int64_t a, void* p, FactorWs* o, int prec) {
@@ -72,11 +72,21 @@ size_t selinv_ws(int64_t n, int64_t b, int64_t a, void* p, SelinvWs* o, int prec
   return c.off;
 }
 
-size_t solve_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, SolveWs* o) {
+// Order of the diagonal sub-blocks of L_ii that the solve inverts: b itself up
+// to 256, else 256 (ceil(b / 256) sub-blocks, the last one ragged).
+inline int64_t solve_sub(int64_t b) { return b < 256 ? b : 256; }
+
+// with_inverses: space for the inverses of the diagonal sub-blocks (the
+// standalone solve forms them; the one-call forms use the selected inversion's
+// L_ii^{-1} instead).
+size_t solve_ws(int64_t n, int64_t b, int64_t a, int64_t R, void* p, SolveWs* o,
+                bool with_inverses = true) {
   Carver c(p);
   SolveWs w;
+  const int64_t ds = solve_sub(b), nsb = (b + ds - 1) / ds;
   w.partial = c.take((size_t)(arrow_chunks(n) * a * R + 1));
-  w.dinv = c.take((size_t)(n * ((b + T - 1) / T) * T * T));
+  w.dinv = with_inverses ? c.take((size_t)(n * nsb * ds * ds)) : nullptr;
+  w.tmp = c.take((size_t)(b * R));
   if (o) *o = w;
   return c.off;
 }
@@ -144,8 +154,11 @@ struct TcWs {
 
 // Runs a (one- or two-term) GEMM. In a tensor-core precision mode an eligible
 // product goes to gemm_tc (two terms concatenated along k there); otherwise the
-// FP64 DMMA kernels run it.
-cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaStream_t s) {
+// FP64 DMMA kernels run it. *used_tc (optional) tells which; reuse_b: op(B) is
+// the one the previous gemm_tc call on tw split (see gemm_tc).
+cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaStream_t s,
+                     bool* used_tc = nullptr, bool reuse_b = false) {
+  if (used_tc) *used_tc = false;
   if (prec == BTA_PREC_FP64 || !routes_to_tc(prec, cls) || !tw.p) return gemm_f64(g, s);
   int kmax = 0, ksum = 0;
   for (int i = 0; i < g.nterms; ++i) {
@@ -155,8 +168,10 @@ cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaS
   // The tensor-core path costs three launches and a splitting pass; it pays for
   // products of at least 2^25 multiply-adds (a 512^3 block product).
   const double macs = (double)g.M * g.N * ksum * g.nb1 * g.nb2;
-  if (g.M >= 64 && g.N >= 64 && kmax >= 64 && macs >= 33554432.0)
-    return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s);
+  if (g.M >= 64 && g.N >= 64 && kmax >= 64 && macs >= 33554432.0) {
+    if (used_tc) *used_tc = true;
+    return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s, reuse_b);
+  }
   return gemm_f64(g, s);
 }
 
@@ -180,6 +195,47 @@ constexpr int64_t kCoopMinB = 128;
 // they take the inverse + tensor-core product, whose cost grows slower than the
 // FP64 solve's b^3 (n=256, b=2048: 2.07 s against 3.64 s).
 constexpr int64_t kHybridMaxB = 1024;
+
+// L_ii = POTRF(A_ii) and Linv = L_ii^{-1} (row stride b) for a block whose
+// triangular solves go to the tensor cores (Ozaki, b > kHybridMaxB), by halves
+// (h = the first half's order, a multiple of the tile):
+//   L11 = POTRF(A11), L11^{-1};  L21 = A21 L11^{-T};  A22 -= L21 L21^T;
+//   L22 = POTRF(A22), L22^{-1};  (L^{-1})21 = -L22^{-1} (L21 L11^{-1}).
+// The two POTRFs run on the FP64 step kernel in place (a quarter of the FP64
+// work of one POTRF of order b); the products run on the tensor cores.
+int potrf_trtri_halves(double* Di, int64_t b, int64_t info_row0, const FactorWs& w, const TcWs& tw,
+                       int prec, cudaStream_t s) {
+  const int64_t h = (b / 2) / T * T, m = b - h;
+  double* A11 = Di;
+  double* A21 = Di + h * b;
+  double* A22 = Di + h * b + h;
+  double* I11 = w.Linv;
+  double* I21 = w.Linv + h * b;
+  double* I22 = w.Linv + h * b + h;
+  HookCtx hc{tw, prec};
+  BTA_TRY(factor_step_coop(A11, nullptr, nullptr, nullptr, nullptr, nullptr, (int)h, 0, 0, info_row0,
+                           w.coop, s, 1, b));
+  BTA_TRY(trtri_blocks(A11, b, b * b, I11, b, b * b, 1, (int)h, s, trtri_hook, &hc));
+  // L21 = A21 L11^{-T} (via W), then A22 -= L21 L21^T (lower tiles)
+  BTA_TRY(gemm_run(one_term(term(A21, b, OP_N, TRI_NONE, I11, b, OP_T, TRI_UPPER, (int)h, 1.0), w.W, b,
+                            (int)m, (int)h, 0.0, 0), CLS_TRSM, tw, prec, s));
+  BTA_TRY(cudaMemcpy2DAsync(A21, b * sizeof(double), w.W, b * sizeof(double), h * sizeof(double), m,
+                            cudaMemcpyDeviceToDevice, s));
+  BTA_TRY(gemm_run(one_term(term(A21, b, OP_N, TRI_NONE, A21, b, OP_T, TRI_NONE, (int)h, -1.0), A22, b,
+                            (int)m, (int)m, 1.0, 1), CLS_SCHUR, tw, prec, s));
+  BTA_TRY(factor_step_coop(A22, nullptr, nullptr, nullptr, nullptr, nullptr, (int)m, 0, 0, info_row0 + h,
+                           w.coop, s, 1, b));
+  BTA_TRY(trtri_blocks(A22, b, b * b, I22, b, b * b, 1, (int)m, s, trtri_hook, &hc));
+  // (L^{-1})21 = -L22^{-1} (L21 L11^{-1})
+  BTA_TRY(gemm_run(one_term(term(A21, b, OP_N, TRI_NONE, I11, b, OP_N, TRI_LOWER, (int)h, 1.0), w.W, b,
+                            (int)m, (int)h, 0.0, 0), CLS_TRSM, tw, prec, s));
+  BTA_TRY(gemm_run(one_term(term(I22, b, OP_N, TRI_LOWER, w.W, b, OP_N, TRI_NONE, (int)m, -1.0), I21, b,
+                            (int)m, (int)h, 0.0, 0), CLS_TRSM, tw, prec, s));
+  // strict upper triangles: L_ii and L_ii^{-1} are lower triangular
+  BTA_TRY(cudaMemset2DAsync(Di + h, b * sizeof(double), 0, m * sizeof(double), h, s));
+  BTA_TRY(cudaMemset2DAsync(w.Linv + h, b * sizeof(double), 0, m * sizeof(double), h, s));
+  return 0;
+}
 
 int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
                 double* tip, const FactorWs& w, int prec, cudaStream_t s, bool coop = true) {
@@ -229,13 +285,18 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   }
   for (int64_t i = 0; i < n; ++i) {
     double* Di = diag + i * bb;
-    if (coop && b >= kCoopMinB)  // the step kernel on A_ii alone: one cooperative POTRF
-      BTA_TRY(factor_step_coop(Di, nullptr, nullptr, nullptr, nullptr, nullptr, B, 0, 0, i * b,
-                               w.coop, s));
-    else
-      BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
     HookCtx hc{tw, prec};
-    BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
+    if (coop && b >= 2 * kCoopMinB && routes_to_tc(prec, CLS_TRSM)) {
+      const int rc = potrf_trtri_halves(Di, b, i * b, w, tw, prec, s);
+      if (rc) return rc;
+    } else {
+      if (coop && b >= kCoopMinB)  // the step kernel on A_ii alone: one cooperative POTRF
+        BTA_TRY(factor_step_coop(Di, nullptr, nullptr, nullptr, nullptr, nullptr, B, 0, 0, i * b,
+                                 w.coop, s));
+      else
+        BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
+      BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
+    }
     if (i + 1 < n) {
       double* Li = lower + i * bb;
       // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
@@ -271,13 +332,17 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
 // lower[i] and arrow[i] hold their final X blocks (enqueue-time hook).
 typedef cudaError_t (*StepHook)(int64_t i, void* ctx);
 
-// before_write (called with i = -1) runs once the prologue has formed every
-// product that only reads L (L_ii^{-1}, G_i, H_i), before the first write into
-// the factor's blocks (M_i into diag, X_nn into the tip).
+// on_linv (called with i = -1) runs as soon as every L_ii^{-1} is in w.Linv (it
+// stays there until the call returns). before_write (i = -1) runs after M_i has
+// been written into diag and before the first write into the tip, lower or arrow
+// blocks (X_nn, then the backward sweep): work that reads the factor's lower,
+// arrow and tip blocks and the inverses, but not diag, may run on another stream
+// between the two.
 int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, double* arrow,
                 double* tip, const SelinvWs& w, int prec, cudaStream_t s,
                 StepHook after = nullptr, void* after_ctx = nullptr,
-                StepHook before_write = nullptr, void* bw_ctx = nullptr) {
+                StepHook before_write = nullptr, void* bw_ctx = nullptr,
+                StepHook on_linv = nullptr, void* ol_ctx = nullptr) {
   const int B = (int)b, Aa = (int)a;
   const int64_t bb = b * b, ab = a * b;
   TcWs tw;
@@ -286,6 +351,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
   // Prologue, independent over i: L_ii^{-1}, G_i, H_i, M_i; then X_nn.
   HookCtx hc{tw, prec};
   BTA_TRY(trtri_blocks(diag, b, bb, w.Linv, b, bb, (int)n, B, s, trtri_hook, &hc));
+  if (on_linv) BTA_TRY(on_linv(-1, ol_ctx));
   if (n > 1) {
     GemmArgs g = one_term(term(lower, b, OP_N, TRI_NONE, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           w.G, b, B, B, 0.0, 0);
@@ -298,13 +364,13 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     g.t[0].sA1 = ab; g.t[0].sB1 = bb; g.sC1 = ab; g.nb1 = (int)n;
     BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
-  if (before_write) BTA_TRY(before_write(-1, bw_ctx));
   {
     GemmArgs g = one_term(term(w.Linv, b, OP_T, TRI_UPPER, w.Linv, b, OP_N, TRI_LOWER, B, 1.0),
                           diag, b, B, B, 0.0, 1);
     g.t[0].sA1 = bb; g.t[0].sB1 = bb; g.sC1 = bb; g.nb1 = (int)n;
     BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
   }
+  if (before_write) BTA_TRY(before_write(-1, bw_ctx));
   if (a > 0) {
     BTA_TRY(trtri_blocks(tip, a, a * a, w.LtInv, a, a * a, 1, Aa, s));
     BTA_TRY(gemm_run(one_term(term(w.LtInv, a, OP_T, TRI_UPPER, w.LtInv, a, OP_N, TRI_LOWER, Aa,
@@ -316,6 +382,9 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
     double* Di = diag + i * bb;
     const double* Gi = w.G + i * bb;
     const double* Hi = w.H + i * ab;
+    // X_{i+1,i} and X_ii share op(B) = [G_i; H_i]: on the tensor cores the second
+    // product reuses the first one's split of it.
+    bool b_split = false;
     if (i + 1 < n) {
       // X_{i+1,i} = -X_{i+1,i+1} G_i - X_{n,i+1}^T H_i
       GemmArgs g = one_term(term(Di + bb, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0),
@@ -324,7 +393,7 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, &b_split));
     }
     if (a > 0) {
       // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i
@@ -334,7 +403,9 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         g.t[1] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
         g.nterms = 2;
       }
-      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
+      bool tc = false;
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, &tc));
+      if (tc) b_split = false;  // that product used the workspace too
     }
     // X_ii = M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i  (lower tiles, then mirrored)
     GemmArgs g{};
@@ -343,27 +414,49 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       g.t[g.nterms++] = term(lower + i * bb, b, OP_T, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
     if (a > 0)
       g.t[g.nterms++] = term(arrow + i * ab, b, OP_T, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0);
-    if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s));
+    if (g.nterms) BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, nullptr, b_split));
     BTA_TRY(mirror_lower(Di, b, bb, 1, B, s));
     if (after) BTA_TRY(after(i, after_ctx));
   }
   return 0;
 }
 
+// Standalone solve (block forward / backward substitution over the pattern).
+// Inside a block the triangular solve is blocked by the diagonal sub-blocks of
+// order ds = min(b, 256): their inverses D_ij are formed first (one batched
+// TRTRI per sub-block column), then each sub-step is two matrix-vector products
+// that spread over the whole GPU: y_j = D_ij t_j and, right-looking, the rows
+// below (forward) or above (backward) take the update from y_j. A block step
+// thus has ceil(b / 256) dependent sub-steps instead of one per 32-row tile.
 int solve_impl(int64_t n, int64_t b, int64_t a, const double* diag, const double* lower,
                const double* arrow, const double* tip, double* rhs, int64_t R,
                const SolveWs& w, cudaStream_t s) {
   const int B = (int)b, Rr = (int)R;
   const int64_t bb = b * b, bR = b * R;
+  const int64_t ds = solve_sub(b), nsb = (b + ds - 1) / ds, dss = ds * ds;
   double* rn = rhs + n * bR;
-  // Inverses of the T x T diagonal tiles of every L_ii, shared by both sweeps.
-  const int64_t dstride = ((b + T - 1) / T) * T * T;
-  BTA_TRY(tile_inverses(diag, b, bb, (int)n, B, w.dinv, s));
+  for (int64_t j = 0; j < nsb; ++j) {
+    const int64_t o = j * ds, sz = std::min(ds, b - o);
+    BTA_TRY(trtri_blocks(diag + o * (b + 1), b, bb, w.dinv + j * dss, ds, nsb * dss, (int)n, (int)sz, s));
+  }
   for (int64_t i = 0; i < n; ++i) {
+    const double* Li = diag + i * bb;
+    const double* Di = w.dinv + i * nsb * dss;
+    double* yi = rhs + i * bR;
+    // t = r_i - L_{i,i-1} y_{i-1}
     if (i > 0)
-      BTA_TRY(gemv_multi(lower + (i - 1) * bb, b, OP_N, B, B, rhs + (i - 1) * bR, R,
-                         rhs + i * bR, R, Rr, -1.0, s));
-    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, false, s, w.dinv + i * dstride));
+      BTA_TRY(gemv_multi(lower + (i - 1) * bb, b, OP_N, B, B, rhs + (i - 1) * bR, R, w.tmp, R, Rr, -1.0, s,
+                         1.0, yi));
+    else
+      BTA_TRY(cudaMemcpyAsync(w.tmp, yi, bR * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int64_t j = 0; j < nsb; ++j) {
+      const int64_t o = j * ds, sz = std::min(ds, b - o);
+      BTA_TRY(gemv_multi(Di + j * dss, ds, OP_N, (int)sz, (int)sz, w.tmp + o * R, R, yi + o * R, R, Rr, 1.0, s,
+                         0.0, nullptr, TRI_LOWER));
+      if (o + sz < b)  // t(o+sz:) -= L_ii(o+sz:, o:o+sz) y_i(o:o+sz)
+        BTA_TRY(gemv_multi(Li + (o + sz) * b + o, b, OP_N, (int)(b - o - sz), (int)sz, yi + o * R, R,
+                           w.tmp + (o + sz) * R, R, Rr, -1.0, s));
+    }
   }
   if (a > 0) {
     BTA_TRY(arrow_gather(arrow, n, b, a, rhs, Rr, w.partial, arrow_chunks(n), rn, s));
@@ -372,10 +465,63 @@ int solve_impl(int64_t n, int64_t b, int64_t a, const double* diag, const double
     BTA_TRY(arrow_scatter(arrow, n, b, a, rn, Rr, rhs, s));
   }
   for (int64_t i = n - 1; i >= 0; --i) {
+    const double* Li = diag + i * bb;
+    const double* Di = w.dinv + i * nsb * dss;
+    double* xi = rhs + i * bR;
+    // t = y_i - L_{i+1,i}^T x_{i+1} (the arrow term is already subtracted)
     if (i + 1 < n)
-      BTA_TRY(gemv_multi(lower + i * bb, b, OP_T, B, B, rhs + (i + 1) * bR, R, rhs + i * bR, R,
-                         Rr, -1.0, s));
-    BTA_TRY(trsv_lower(diag + i * bb, b, B, rhs + i * bR, R, Rr, true, s, w.dinv + i * dstride));
+      BTA_TRY(gemv_multi(lower + i * bb, b, OP_T, B, B, rhs + (i + 1) * bR, R, w.tmp, R, Rr, -1.0, s, 1.0,
+                         xi));
+    else
+      BTA_TRY(cudaMemcpyAsync(w.tmp, xi, bR * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int64_t j = nsb - 1; j >= 0; --j) {
+      const int64_t o = j * ds, sz = std::min(ds, b - o);
+      BTA_TRY(gemv_multi(Di + j * dss, ds, OP_T, (int)sz, (int)sz, w.tmp + o * R, R, xi + o * R, R, Rr, 1.0, s,
+                         0.0, nullptr, TRI_LOWER));
+      if (o > 0)  // t(:o) -= L_ii(o:o+sz, :o)^T x_i(o:o+sz)
+        BTA_TRY(gemv_multi(Li + o * b, b, OP_T, (int)o, (int)sz, xi + o * R, R, w.tmp, R, Rr, -1.0, s));
+    }
+  }
+  return 0;
+}
+
+// The solve with the block inverses Linv_i = L_ii^{-1} at hand (formed by the
+// selected inversion's prologue): every block step is two bandwidth-bound
+// products instead of a chain of triangular tile solves, and L_ii itself is not
+// read. Forward: y_i = Linv_i (r_i - L_{i,i-1} y_{i-1}); y_n = L_nn^{-1}(r_n -
+// sum_i L_{n,i} y_i). Backward: x_n = L_nn^{-T} y_n; x_i = Linv_i^T (y_i -
+// L_{i+1,i}^T x_{i+1} - L_{n,i}^T x_n). Reads lower, arrow, tip (L_nn) and Linv.
+int solve_inv_impl(int64_t n, int64_t b, int64_t a, const double* lower, const double* arrow,
+                   const double* tip, const double* Linv, double* rhs, int64_t R, const SolveWs& w,
+                   cudaStream_t s) {
+  const int B = (int)b, Rr = (int)R;
+  const int64_t bb = b * b, bR = b * R;
+  double* rn = rhs + n * bR;
+  for (int64_t i = 0; i < n; ++i) {
+    // tmp = r_i - L_{i,i-1} y_{i-1}; y_i = Linv_i tmp
+    if (i > 0)
+      BTA_TRY(gemv_multi(lower + (i - 1) * bb, b, OP_N, B, B, rhs + (i - 1) * bR, R, w.tmp, R, Rr, -1.0,
+                         s, 1.0, rhs + i * bR));
+    else
+      BTA_TRY(cudaMemcpyAsync(w.tmp, rhs, bR * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BTA_TRY(gemv_multi(Linv + i * bb, b, OP_N, B, B, w.tmp, R, rhs + i * bR, R, Rr, 1.0, s, 0.0,
+                       nullptr, TRI_LOWER));
+  }
+  if (a > 0) {
+    BTA_TRY(arrow_gather(arrow, n, b, a, rhs, Rr, w.partial, arrow_chunks(n), rn, s));
+    BTA_TRY(trsv_lower(tip, a, (int)a, rn, R, Rr, false, s));
+    BTA_TRY(trsv_lower(tip, a, (int)a, rn, R, Rr, true, s));
+    BTA_TRY(arrow_scatter(arrow, n, b, a, rn, Rr, rhs, s));
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    // tmp = y_i - L_{i+1,i}^T x_{i+1} (the arrow term is already subtracted); x_i = Linv_i^T tmp
+    if (i + 1 < n)
+      BTA_TRY(gemv_multi(lower + i * bb, b, OP_T, B, B, rhs + (i + 1) * bR, R, w.tmp, R, Rr, -1.0, s,
+                         1.0, rhs + i * bR));
+    else
+      BTA_TRY(cudaMemcpyAsync(w.tmp, rhs + i * bR, bR * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BTA_TRY(gemv_multi(Linv + i * bb, b, OP_T, B, B, w.tmp, R, rhs + i * bR, R, Rr, 1.0, s, 0.0,
+                       nullptr, TRI_LOWER));
   }
   return 0;
 }
@@ -817,7 +963,7 @@ size_t pipe_ws(int64_t n, int64_t b, int64_t a, int64_t R, bool host, void* p, P
   region = std::max(region, logdet_ws(n, sub, &w.lw));
   c.off += align_up(region);
   if (R > 0) {
-    const size_t vsz = solve_ws(n, b, a, R, p ? (char*)p + c.off : nullptr, &w.vw);
+    const size_t vsz = solve_ws(n, b, a, R, p ? (char*)p + c.off : nullptr, &w.vw, false);
     c.off += align_up(vsz);
   }
   if (o) *o = w;
@@ -852,6 +998,13 @@ struct PipeCtx {
   cudaEvent_t* evout;
   cudaEvent_t ev_solved;
   bool host, solving;
+  // the solve (R > 0), started once the prologue has formed L_ii^{-1}
+  double *tip, *rhs, *x_host;
+  int64_t R;
+  const SolveWs* vw;
+  const double* linv;
+  cudaStream_t cs;
+  cudaEvent_t ev_linv;
 };
 
 // Blocks [i, i + C) are final: copy them back on the copy-out stream.
@@ -875,10 +1028,32 @@ cudaError_t pipe_after_step(int64_t i, void* ctx) {
   return e;
 }
 
-// The selected inversion's first write into the factor: the solve must be done.
+// The selected inversion's first write into the blocks the solve reads (tip,
+// lower, arrow): the solve must be done.
 cudaError_t pipe_before_write(int64_t, void* ctx) {
   PipeCtx& h = *(PipeCtx*)ctx;
   return h.solving ? cudaStreamWaitEvent(h.s, h.ev_solved, 0) : cudaSuccess;
+}
+
+// Every L_ii^{-1} is formed: the solve runs on the side stream, beside the rest
+// of the prologue, and the solution goes back to the host once it is done.
+cudaError_t pipe_solve(int64_t, void* ctx) {
+  PipeCtx& h = *(PipeCtx*)ctx;
+  if (!h.solving) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(h.ev_linv, h.s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h.cs, h.ev_linv, 0);
+  if (e != cudaSuccess) return e;
+  const int rc = solve_inv_impl(h.n, h.b, h.a, h.lower, h.arrow, h.tip, h.linv, h.rhs, h.R, *h.vw, h.cs);
+  if (rc) return rc > 0 ? (cudaError_t)rc : cudaErrorInvalidValue;
+  e = cudaEventRecord(h.ev_solved, h.cs);
+  if (e != cudaSuccess) return e;
+  if (h.host) {
+    e = cudaStreamWaitEvent(h.cout, h.ev_solved, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.x_host, h.rhs, (h.n * h.b + h.a) * h.R * sizeof(double), cudaMemcpyDeviceToHost,
+                          h.cout);
+  }
+  return e;
 }
 
 // Host mode: h* are host inputs, x* host outputs, the blocks live in w's device
@@ -965,24 +1140,11 @@ int pipeline_impl(int64_t n, int64_t b, int64_t a, int64_t R, const PipeArgs& io
   }
   BTA_TRY(logdet_f64(diag, n, b, tip, a, w.lw.partial, ld, s));
   if (io.host) BTA_TRY(cudaMemcpyAsync(io.hld, ld, sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (R > 0) {
-    // The solve on the side stream, concurrent with the selinv prologue.
-    BTA_TRY(cudaEventRecord(ev_factored, s));
-    BTA_TRY(cudaStreamWaitEvent(cs, ev_factored, 0));
-    const int rc = solve_impl(n, b, a, diag, lower, arrow, tip, rhs, R, w.vw, cs);
-    if (rc) return rc;
-    BTA_TRY(cudaEventRecord(ev_solved, cs));
-    if (io.host) {
-      BTA_TRY(cudaStreamWaitEvent(cout, ev_solved, 0));
-      BTA_TRY(cudaMemcpyAsync(io.x, rhs, (n * b + a) * R * sizeof(double), cudaMemcpyDeviceToHost,
-                              cout));
-    }
-  }
   PipeCtx hp{n, b, a, C, diag, lower, arrow, io.xd, io.xl, io.xa, s, cout, evout, ev_solved,
-             io.host, R > 0};
+             io.host, R > 0, tip, rhs, io.x, R, &w.vw, w.sw.Linv, cs, ev_factored};
   {
     const int rc = selinv_impl(n, b, a, diag, lower, arrow, tip, w.sw, prec, s, pipe_after_step, &hp,
-                               pipe_before_write, &hp);
+                               pipe_before_write, &hp, pipe_solve, &hp);
     if (rc) return rc;
   }
   if (io.host) {

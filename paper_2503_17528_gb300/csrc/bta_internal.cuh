@@ -81,23 +81,26 @@ double gemm_alg_flops(const GemmArgs& g);
 cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
                          long long info_row0, long long info_rstride,
                          cudaStream_t s);
-// Scratch of the cooperative factor-step kernel, 256-byte aligned.
-constexpr size_t kCoopScratch = 32768;
 // Largest tile counts of the fused factor step (b, a <= 32768): tiles per block
-// order and extended rows (two blocks plus the arrowhead). Its per-launch
-// counters and flags sit from byte 1016 of the same scratch.
+// order and extended rows (two blocks plus the arrowhead).
 constexpr int kStepMaxTiles = 1024;
 constexpr int kStepMaxExtTiles = 3 * 1024;
-static_assert(1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int) <= kCoopScratch,
-              "step scratch");
+// Scratch of the cooperative factor-step kernel, 256-byte aligned: one flag word
+// per extended tile row and one counter per factor column, then 32 pivot
+// reciprocals per diagonal tile.
+constexpr size_t kStepFlagBytes = 16384;
+constexpr size_t kCoopScratch = kStepFlagBytes + (size_t)kStepMaxTiles * 32 * sizeof(double);
+static_assert((kStepMaxExtTiles + kStepMaxTiles) * sizeof(int) <= kStepFlagBytes, "step scratch");
 // One block step of the factorization in one cooperative launch: L_ii, L_{i+1,i}
 // and L_{n,i} in place, and (schur != 0) the Schur updates of A_{i+1,i+1},
 // A_{n,i+1} and the tip (lower tiles). next == 0 for the last block (Lw, D1, Ar1
 // unused); a == 0: no arrowhead; schur == 0: D1, Ar1 and tip are unused.
-// scratch: kCoopScratch bytes, 256-byte aligned.
+// scratch: kCoopScratch bytes, 256-byte aligned. ld (0: b) is the row stride of
+// D0, Lw and D1, so a diagonal sub-block of a larger matrix can be factored in
+// place; the arrow blocks keep rows of b.
 cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
                              double* tip, int b, int a, int next, long long info_row0,
-                             void* scratch, cudaStream_t s, int schur = 1);
+                             void* scratch, cudaStream_t s, int schur = 1, int64_t ld = 0);
 // Reads and clears the timeout flag of the cooperative kernels' grid barriers.
 cudaError_t wait_error_read_reset(int* out);
 // Enqueues one CTA that waits on *flag_dev (never raised) for `polls` polls.
@@ -129,19 +132,17 @@ cudaError_t logdet_combine(const double* p1, int64_t n1, const double* p2, int64
 cudaError_t axpy_f64(int64_t n, double alpha, const double* x, double* y, cudaStream_t s);
 
 // Solve pieces (rhs row-major [rows][R]).
-// Inverses of the T x T diagonal tiles of `count` lower-triangular blocks
-// (order nrow, stride sl), packed as D[block][tile][T][T].
-cudaError_t tile_inverses(const double* L, int64_t ld, int64_t sl, int count, int nrow,
-                          double* D, cudaStream_t s);
-// x <- L^{-1} x (trans: L^{-T} x) by one thread-block cluster; Dinv (optional):
-// L's packed diagonal-tile inverses, which replace the per-tile substitution.
+// x <- L^{-1} x (trans: L^{-T} x) by one thread-block cluster (tile substitution;
+// used for the arrow tip).
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x,
-                       int64_t ldx, int R, bool trans, cudaStream_t s,
-                       const double* Dinv = nullptr);
-// x[M][R] += alpha * op(A) * y[K][R], op(A) is M x K.
+                       int64_t ldx, int R, bool trans, cudaStream_t s);
+// x[M][R] = beta * xin + alpha * op(A) * y[K][R], op(A) is M x K; xin defaults
+// to x (x += alpha op(A) y for beta = 1). triA = TRI_LOWER: the stored A is lower
+// triangular and its zero part is not read.
 cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K,
                        const double* y, int64_t ldy, double* x, int64_t ldx,
-                       int R, double alpha, cudaStream_t s);
+                       int R, double alpha, cudaStream_t s, double beta = 1.0,
+                       const double* xin = nullptr, int triA = TRI_NONE);
 // r_n[a][R] -= sum_i arrow[i] (a x b) * y_i (b x R), y_i = rhs block i.
 cudaError_t arrow_gather(const double* arrow, int64_t n, int64_t b, int64_t a,
                          const double* rhs, int R, double* partial,

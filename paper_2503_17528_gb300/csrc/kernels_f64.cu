@@ -585,67 +585,14 @@ __global__ void __launch_bounds__(256) tile_inv_kernel(const double* L, int64_t 
                 Li + (int64_t)blockIdx.y * si + (int64_t)o * ldi + o, ldi, tb);
 }
 
-// The same inverses packed as [block][tile][T][T] (entries beyond a ragged last
-// tile's order are left unwritten).
-__global__ void __launch_bounds__(256) tile_inv_packed_kernel(const double* L, int64_t ld,
-                                                              int64_t sl, double* D, int nrow) {
-  const int nt = (nrow + T - 1) / T, o = blockIdx.x * T, tb = min(T, nrow - o);
-  tile_inv_body(L + (int64_t)blockIdx.y * sl + (int64_t)o * ld + o, ld,
-                D + ((int64_t)blockIdx.y * nt + blockIdx.x) * T * T, T, tb);
-}
-
-cudaError_t tile_inverses(const double* L, int64_t ld, int64_t sl, int count, int nrow,
-                          double* D, cudaStream_t s) {
-  if (count <= 0 || nrow <= 0) return cudaSuccess;
-  const int nt = (nrow + T - 1) / T;
-  for (int c0 = 0; c0 < count; c0 += 65535) {
-    const int cnt = min(65535, count - c0);
-    TimedLaunch tl(K_TILE_INV, 0.0, s);
-    tile_inv_packed_kernel<<<dim3(nt, cnt), 256, 0, s>>>(L + (int64_t)c0 * sl, ld, sl,
-                                                         D + (int64_t)c0 * nt * T * T, nrow);
-  }
-  return cudaGetLastError();
-}
-
 static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// Cooperative-launch building blocks. The grid barrier counts arrivals and
-// releases a generation word; a wait that exceeds its poll limit records the
-// timeout and lets the CTA go on, so a kernel always ends (the caller reads the
-// flag with bta_tc_status).
+// Cooperative-launch building blocks. A wait that exceeds its poll limit
+// records the timeout and lets the CTA go on, so a kernel always ends (the
+// caller reads the flag with bta_tc_status).
 // ---------------------------------------------------------------------------
 __device__ int g_wait_error;
-
-struct CoopBar {
-  unsigned int count;
-  unsigned int gen;
-};
-
-__device__ __forceinline__ void grid_barrier(CoopBar* bar, unsigned nblocks, unsigned& gen) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g0 = gen;
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      unsigned polls = 0;
-      while (atomicAdd(&bar->gen, 0u) == g0) {
-        if (++polls > (1u << 24)) {
-          atomicExch(&g_wait_error, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    gen = g0 + 1;
-  }
-  __syncthreads();
-}
 
 // Row of the lower-triangular index u (u = row (row + 1) / 2 + col, col <= row).
 __device__ __forceinline__ int tri_row(int u) {
@@ -723,14 +670,31 @@ __device__ void coop_factor(double (*S)[T + 1], double* rd, int tb, long long ro
 //   A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T,  A_{n,i+1} -= L_{n,i} L_{i+1,i}^T,
 //   A_nn -= L_{n,i} L_{n,i}^T.
 // Tiles are indexed over the "extended" rows: the tiles of block i, then those
-// of block i+1, then the arrow rows. At tile step k (a column of block i):
-//   A. 16-row slices of every tile (r, k), r > k, solve X L_kk^T = A(r, k)
-//      (this covers the POTRF panel, the TRSM of L_{i+1,i} and of L_{n,i});
-//   B. every lower tile (r, c), r >= c > k, takes -= L(r,k) L(c,k)^T; CTA 0
-//      takes tile (k+1, k+1) first and factors it (look-ahead).
-// The TRSM needs no inverse of L_ii, and the Schur products run as part of the
-// same tile sweep, so the latency-bound tile steps of the POTRF overlap with
-// the bulk of the step's work.
+// of block i+1, then the arrow rows (E in all); the columns are those of block
+// i (nt, factored here) and, with the Schur updates on, those of block i+1 and
+// the tip (updated only). Operations on a tile (r, c):
+//   U(r, c, k)  tile (r, c) -= L(r, k) L(c, k)^T, for every factor column k < c;
+//   F(r, c)     (c < nt, after every U) tile (c, c) -> its Cholesky factor, or
+//               tile (r, c), r > c -> the panel solve X L(c, c)^T = A(r, c).
+// This covers the POTRF of A_ii, the TRSMs of L_{i+1,i} and L_{n,i} (panel
+// solves, no inverse of L_ii) and the three Schur products (the U's in the
+// columns of block i+1 and of the tip).
+//
+// Scheduling is dataflow, without grid barriers. Tile (r, c) always belongs to
+// CTA u(r, c) mod G, u being the tile's column-major index in the lower
+// triangle, so every update of a tile runs on one CTA in program order. The
+// only waits are on finalized tiles: pdone[r] counts the finalized columns of
+// tile row r (tile (r, c) is final once pdone[r] > c). Each CTA walks phases
+//   1(k) = U(., k+1, k) then F(., k+1);  2(k) = U(., k+2, k);  3(k) = U(., c >= k+3, k)
+// in the order 1(k), 2(k), 1(k+1), 3(k), 2(k+1), 1(k+2), 3(k+1), ... (phase
+// numbers 3k, 3k+2 and 3k+4), taking its own tiles of each phase in column-major
+// order. Column k+2 is thus finalized before the bulk of step k: a two-step
+// look-ahead. Every wait is on a tile of an earlier phase, or (the panel solves
+// of F(., k+1)) on the diagonal tile (k+1, k+1), which its owner takes first in
+// the same phase and which waits on earlier phases only; so the schedule cannot
+// deadlock while all CTAs are resident (cooperative launch). Every wait is
+// bounded and reports through bta_tc_status. The bulk phase 3(k) is one
+// contiguous range of u, so its tiles split evenly over the CTAs.
 // ---------------------------------------------------------------------------
 constexpr int kStepThreads = 256;
 
@@ -742,15 +706,12 @@ struct StepArgs {
   double* Ar1;  // A_{n,i+1} (a x b): updated; unused when next == 0
   double* tip;  // A_nn (a x a): lower tiles updated
   int b, a, nt, na, next;
+  int64_t ld;      // leading dimension of D0, Lw and D1 (b for whole blocks)
   int schur;       // 0: only block i's columns (no updates of D1, Ar1, tip)
   long long row0;  // 1-based global row of block i's first row, minus one
-  CoopBar* bar;
-  double* rdiag;  // [2][T]: 1 / L_jj of the current diagonal tile (by step parity)
-  int* ctr;       // [nt]: items taken so far in step k
-  int* lflag;     // = k + 1 once tile (k+1, k+1) is factored in step k
-  int* colflag;   // [extended rows]: = k + 1 once tile (r, k+1) has its step-k update
-                  // (all three zeroed per launch)
-  int* smid0;     // SM of CTA 0
+  int* pdone;      // [E]: finalized columns of each extended tile row (zeroed per launch)
+  int* colcnt;     // [nt]: finalized tiles of each factor column (zeroed per launch)
+  double* rdv;     // [nt][T]: 1 / L_jj of each factored diagonal tile
 };
 
 // Group of an extended tile row (0: block i, 1: block i+1, 2: arrow) and its
@@ -778,7 +739,8 @@ __device__ __forceinline__ int ext_rows(const StepArgs& p, int r) {
   return min(T, (g == 2 ? p.a : p.b) - T * lr);
 }
 
-// Address and leading dimension of tile (r, c), r >= c, of the extended lower triangle.
+// Address and leading dimension of tile (r, c), r >= c, of the extended lower
+// triangle (arrow rows have rows of b, the tip rows of a, the rest rows of ld).
 __device__ __forceinline__ double* ext_tile(const StepArgs& p, int r, int c, int64_t& ld) {
   int lr, lc;
   const int gr = ext_group(p, r, lr), gc = ext_group(p, c, lc);
@@ -786,26 +748,14 @@ __device__ __forceinline__ double* ext_tile(const StepArgs& p, int r, int c, int
     ld = p.a;
     return p.tip + (int64_t)(T * lr) * p.a + T * lc;
   }
-  ld = p.b;
-  double* base;
-  if (gc == 0)
-    base = gr == 0 ? p.D0 : (gr == 1 ? p.Lw : p.Ar0);
-  else
-    base = gr == 1 ? p.D1 : p.Ar1;
-  return base + (int64_t)(T * lr) * p.b + T * lc;
+  if (gr == 2) {
+    ld = p.b;
+    return (gc == 0 ? p.Ar0 : p.Ar1) + (int64_t)(T * lr) * p.b + T * lc;
+  }
+  ld = p.ld;
+  double* base = gc == 0 ? (gr == 0 ? p.D0 : p.Lw) : p.D1;
+  return base + (int64_t)(T * lr) * p.ld + T * lc;
 }
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
-               "r"(pred ? 8 : 0));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
 
 // Panel solve in shared memory: X (rows x tb) <- X L^{-T}, L lower in Lt, rdv = 1 / diag(L).
 __device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*Lt)[T + 1],
@@ -824,13 +774,31 @@ __device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*L
 }
 
 // Bounded wait until *flag >= v (a flag another CTA of the same cooperative
-// launch raises); after max_polls polls the error word is set and the CTA goes on.
+// launch raises); after max_polls polls the error word is set and the CTA goes
+// on. Once any wait has timed out, later waits give up at once, so a launch that
+// lost a dependency still ends within about one timeout.
 __device__ __forceinline__ void wait_flag_ge(const int* flag, int v,
-                                             unsigned max_polls = 1u << 24) {
+                                             unsigned max_polls = 1u << 22) {
   if (threadIdx.x == 0) {
     unsigned polls = 0;
     while (atomicAdd((int*)flag, 0) < v) {
-      if (++polls > max_polls) {
+      if (++polls > max_polls || *(volatile int*)&g_wait_error) {
+        atomicExch(&g_wait_error, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Bounded wait until flag_a >= va and flag_b >= vb (same rules as wait_flag_ge).
+__device__ __forceinline__ void wait_flags_ge(const int* fa, int va, const int* fb, int vb) {
+  if (threadIdx.x == 0) {
+    unsigned polls = 0;
+    while (atomicAdd((int*)fa, 0) < va || atomicAdd((int*)fb, 0) < vb) {
+      if (++polls > (1u << 22) || *(volatile int*)&g_wait_error) {
         atomicExch(&g_wait_error, 1);
         break;
       }
@@ -850,245 +818,202 @@ __device__ __forceinline__ void raise_flag(int* flag, int v) {
   }
 }
 
+// 8-byte asynchronous global -> shared copy (zero-fill when !pred).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
 __global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p) {
-  __shared__ double S[T][T + 1];   // look-ahead tile (CTA 0) or a panel slice
-  __shared__ double Lt[T][T + 1];  // the diagonal factor the panel slices are solved with
-  __shared__ double Pb[2][T][T + 1];
-  __shared__ double Qb[2][T][T + 1];
+  __shared__ double Pb[2][T][T + 1];  // L(r, k), double-buffered
+  __shared__ double Qb[2][T][T + 1];  // L(c, k)
   __shared__ double rd[T];
-  __shared__ int s_next;
+  // Finalizations run outside the pipelined bulk phase, when buffer 1 is idle:
+  // S (a diagonal tile being factored, or a panel tile being solved) and Lt (the
+  // diagonal factor a panel tile is solved with) live there.
+  double(*const S)[T + 1] = Pb[1];
+  double(*const Lt)[T + 1] = Qb[1];
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
   const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
   const int wm = (warp >> 1) * 8, wn = (warp & 1) * 16;  // this warp's 8 x 16 part of a tile
-  const int nt = p.nt, E = nt * (1 + p.next) + p.na;
-  const int64_t b = p.b;
-  unsigned gen = 0;
+  const int nt = p.nt, E = nt * (1 + p.next) + p.na, Ecol = p.schur ? E : nt;
+  const int64_t b = p.ld;  // row stride of A_ii
 
-  // Prologue: tile (0, 0), then the panel tiles of column 0.
-  unsigned smid;
-  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-  if (bid == 0) {
-    if (tid == 0) *p.smid0 = (int)smid;
-    const int tb = min(T, p.b);
+  // The strict upper tiles of A_ii belong to no operation: zero them now (upper
+  // tile u = (tr, tc), tc > tr, enumerated row by row).
+  for (int u = bid; u < nt * (nt - 1) / 2; u += G) {
+    int tr = 0, rem = u;
+    while (rem >= nt - 1 - tr) rem -= nt - 1 - tr++;
+    const int tc = tr + 1 + rem;
+    const int rows = min(T, p.b - tr * T), cols = min(T, p.b - tc * T);
+    double* Z = p.D0 + (int64_t)(tr * T) * b + tc * T;
+    for (int e = tid; e < T * T; e += blockDim.x)
+      if (e / T < rows && e % T < cols) Z[(int64_t)(e / T) * b + e % T] = 0.0;
+  }
+
+  // Column-major index of the first tile of column c (rows c .. E-1).
+  auto off = [&](int c) -> long long { return (long long)c * E - (long long)c * (c - 1) / 2; };
+
+  // U(r, c, k): tile (r, c) -= L(r, k) L(c, k)^T, in two parts: issue the
+  // copies of the two panel tiles into buffer bf (one commit group), then, once
+  // they have landed, the DMMA update of C in place.
+  auto issue = [&](int r, int c, int k, int bf) {
+    const int tbk = min(T, p.b - k * T);
+    const int rb = ext_rows(p, r), cb = ext_rows(p, c);
+    int64_t ldr, ldq;
+    const double* Lr = ext_tile(p, r, k, ldr);
+    const double* Lc = ext_tile(p, c, k, ldq);
     for (int e = tid; e < T * T; e += blockDim.x) {
       const int i = e / T, j = e % T;
-      S[i][j] = (i < tb && j <= i) ? p.D0[(int64_t)i * b + j] : 0.0;
+      const bool pr = i < rb && j < tbk, pc = i < cb && j < tbk;
+      cp_async8(&Pb[bf][i][j], pr ? Lr + (int64_t)i * ldr + j : Lr, pr);
+      cp_async8(&Qb[bf][i][j], pc ? Lc + (int64_t)i * ldq + j : Lc, pc);
     }
+    cp_async_commit();
+  };
+  auto compute = [&](int r, int c, int bf) {
+    const int rb = ext_rows(p, r), cb = ext_rows(p, c);
+    int64_t ldc;
+    double* C = ext_tile(p, r, c, ldc);
+    const int row = wm + gq;
+    if (wm < rb && wn < cb) {  // warp-uniform
+      double cold[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+      double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int col = wn + ni * 8 + 2 * tq + j;
+          if (row < rb && col < cb) cold[ni][j] = C[(int64_t)row * ldc + col];
+        }
+#pragma unroll
+      for (int ks = 0; ks < T; ks += 4) {
+        const double av = Pb[bf][row][ks + tq];
+        dmma_8x8x4(acc[0], av, Qb[bf][wn + gq][ks + tq]);
+        dmma_8x8x4(acc[1], av, Qb[bf][wn + 8 + gq][ks + tq]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int col = wn + ni * 8 + 2 * tq + j;
+          if (row < rb && col < cb) C[(int64_t)row * ldc + col] = cold[ni][j] - acc[ni][j];
+        }
+    }
+  };
+  // One update with its own waits (the look-ahead columns).
+  auto update = [&](int r, int c, int k) {
+    wait_flags_ge(p.pdone + r, k + 1, p.pdone + c, k + 1);
+    issue(r, c, k, 0);
+    cp_async_wait<0>();
     __syncthreads();
-    coop_factor(S, rd, tb, p.row0);
+    compute(r, c, 0);
+    __syncthreads();  // the buffer is consumed
+  };
+
+  // F(r, c): factor the diagonal tile (r == c) or solve the panel tile (r > c).
+  auto finalize = [&](int r, int c) {
+    const int tb = min(T, p.b - c * T);
+    if (r == c) {
+      double* Dc = p.D0 + (int64_t)(c * T) * b + c * T;
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        S[i][j] = (i < tb && j <= i) ? Dc[(int64_t)i * b + j] : 0.0;
+      }
+      __syncthreads();
+      coop_factor(S, rd, tb, p.row0 + (long long)c * T);
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (i < tb && j < tb) Dc[(int64_t)i * b + j] = S[i][j];
+      }
+      if (tid < T) p.rdv[(int64_t)c * T + tid] = rd[tid];
+      __syncthreads();
+      raise_flag(p.pdone + c, c + 1);
+      if (tid == 0) atomicAdd(p.colcnt + c, 1);
+      return;
+    }
+    wait_flag_ge(p.pdone + c, c + 1);  // the diagonal tile (c, c) is factored
+    const int rows = ext_rows(p, r);
+    int64_t ldx;
+    double* X = ext_tile(p, r, c, ldx);
+    const double* Dc = p.D0 + (int64_t)(c * T) * b + c * T;
     for (int e = tid; e < T * T; e += blockDim.x) {
       const int i = e / T, j = e % T;
-      if (i < tb && j < tb) p.D0[(int64_t)i * b + j] = S[i][j];
+      Lt[i][j] = (i < tb && j <= i) ? __ldcg(Dc + (int64_t)i * b + j) : 0.0;
+      S[i][j] = (i < rows && j < tb) ? X[(int64_t)i * ldx + j] : 0.0;
     }
-    if (tid < T) p.rdiag[tid] = rd[tid];
-  }
-  grid_barrier(p.bar, G, gen);
-  // A CTA on CTA 0's SM takes no tiles during the look-ahead, which then runs
-  // without contention on that SM's FP64 pipe.
-  const bool beside0 = bid != 0 && (int)smid == *(volatile int*)p.smid0;
-  {
-    const int below = E - 1, tb0 = min(T, p.b);
-    const int per = 4 * below <= G ? 4 : (2 * below <= G ? 2 : 1), sh = T / per;
-    bool loaded = false;
-    for (int sl = bid; sl < per * below; sl += G) {
-      const int r = 1 + sl / per, rs = (sl % per) * sh;
-      const int rows = min(sh, ext_rows(p, r) - rs);
-      if (rows <= 0) continue;  // uniform over the CTA
-      int64_t ldx;
-      double* X = ext_tile(p, r, 0, ldx);
-      X += (int64_t)rs * ldx;
-      __syncthreads();
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        if (!loaded) Lt[i][j] = (i < tb0 && j <= i) ? p.D0[(int64_t)i * b + j] : 0.0;
-        S[i][j] = (i < rows && j < tb0) ? X[(int64_t)i * ldx + j] : 0.0;
-      }
-      if (!loaded && tid < T) rd[tid] = p.rdiag[tid];
-      loaded = true;
-      __syncthreads();
-      panel_solve(S, Lt, rd, rows, tb0);
-      for (int e = tid; e < rows * tb0; e += blockDim.x) {
-        const int i = e / tb0, c = e % tb0;
-        X[(int64_t)i * ldx + c] = S[i][c];
-      }
+    if (tid < T) rd[tid] = __ldcg(p.rdv + (int64_t)c * T + tid);
+    __syncthreads();
+    panel_solve(S, Lt, rd, rows, tb);
+    for (int e = tid; e < rows * tb; e += blockDim.x) {
+      const int i = e / tb, j = e % tb;
+      X[(int64_t)i * ldx + j] = S[i][j];
     }
-  }
-  grid_barrier(p.bar, G, gen);
+    __syncthreads();
+    raise_flag(p.pdone + r, c + 1);
+    if (tid == 0) atomicAdd(p.colcnt + c, 1);
+  };
 
-  // Tile step k. Work items, taken in order from a per-step counter:
-  //   1. the tiles (r, k+1), r > k+1: -= L(r,k) L(k+1,k)^T, then flagged;
-  //   2. the other trailing tiles (r, c), r >= c > k+1 (or >= k+1 without look-ahead);
-  //   3. the panel slices of column k+1 (X L_{k+1,k+1}^T = A(r, k+1)), each once
-  //      its tile is flagged and CTA 0 has factored (k+1, k+1).
-  // CTA 0 first factors tile (k+1, k+1) (after its step-k update) and then joins.
-  // Every item waits only on items earlier in the order, held by running CTAs.
-  for (int k = 0; k < nt; ++k) {
-    const int m = E - k - 1;  // extended tiles below k
-    if (m == 0) break;        // last block without arrowhead: nothing trails the last panel
-    const int o = k * T, tbk = min(T, p.b - o);
-    const bool look = k + 1 < nt;
-    const int o1 = o + T, tb1 = look ? min(T, p.b - o1) : 0;
-    if (look && bid == 0) {
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        Pb[0][i][j] = (i < tb1 && j < tbk) ? p.D0[(int64_t)(o1 + i) * b + o + j] : 0.0;
-        S[i][j] = (i < tb1 && j <= i) ? p.D0[(int64_t)(o1 + i) * b + o1 + j] : 0.0;
-      }
-      __syncthreads();
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        if (j <= i && i < tb1) {
-          double acc = 0.0;
-          for (int c = 0; c < tbk; ++c) acc = fma(Pb[0][i][c], Pb[0][j][c], acc);
-          S[i][j] -= acc;
-        }
-      }
-      __syncthreads();
-      coop_factor(S, rd, tb1, p.row0 + o1);
-      for (int e = tid; e < T * T; e += blockDim.x) {
-        const int i = e / T, j = e % T;
-        if (i < tb1 && j < tb1) p.D0[(int64_t)(o1 + i) * b + o1 + j] = S[i][j];
-      }
-      if (tid < T) p.rdiag[((k + 1) & 1) * T + tid] = rd[tid];
-      __syncthreads();
-      raise_flag(p.lflag, k + 1);
+  // This CTA's tiles of column c in rows [c, E), in order.
+  auto column = [&](int c, int k, bool fin) {
+    const long long lo = off(c), hi = lo + (E - c);
+    for (long long u = lo + ((bid - lo % G) % G + G) % G; u < hi; u += G) {
+      const int r = c + (int)(u - lo);
+      if (k >= 0) update(r, c, k);
+      if (fin) finalize(r, c);
     }
-    if (look && beside0) wait_flag_ge(p.lflag, k + 1);
-    const int ncol = look ? m - 1 : 0;                 // category 1
-    const int tri0 = look ? k + 2 : k + 1;
-    // Category 2: the lower triangle over tri0..E-1, or without Schur updates
-    // only its columns of block i: a triangle over tri0..nt-1 and the rectangle
-    // of the later rows under it.
-    const int tm = p.schur ? E - tri0 : max(0, nt - tri0);
-    const int ntri = tm * (tm + 1) / 2;
-    const int nupd = ncol + ntri + (p.schur ? 0 : (E - nt) * tm);  // categories 1 + 2
-    const int per = 2, sh = T / per;                    // category 3: 16-row slices
-    const int nitems = nupd + (look ? per * (m - 1) : 0);
-    int* ctr = p.ctr + k;
-    auto decode = [&](int t, int& r, int& c) {
-      if (t < ncol) {
-        r = k + 2 + t;
-        c = k + 1;
-      } else if (t < ncol + ntri) {
-        const int u = t - ncol, rr = tri_row(u);
-        r = tri0 + rr;
-        c = tri0 + (u - rr * (rr + 1) / 2);
-      } else if (t < nupd) {
-        const int u = t - ncol - ntri;
-        r = nt + u / tm;
-        c = tri0 + u % tm;
-      } else {
-        const int sidx = t - nupd;
-        r = k + 2 + sidx / per;
-        c = (sidx % per) * sh;  // row offset of the slice inside its tile
-      }
-    };
-    auto issue = [&](int t, int bf) {
-      if (t < nupd) {
-        int r, c;
-        decode(t, r, c);
-        const int rb = ext_rows(p, r), cb = ext_rows(p, c);
-        int64_t ldr, ldq;
-        const double* Lr = ext_tile(p, r, k, ldr);
-        const double* Lc = ext_tile(p, c, k, ldq);
-        for (int e = tid; e < T * T; e += blockDim.x) {
-          const int i = e / T, j = e % T;
-          const bool pr = i < rb && j < tbk, pc = i < cb && j < tbk;
-          cp_async8(&Pb[bf][i][j], pr ? Lr + (int64_t)i * ldr + j : Lr, pr);
-          cp_async8(&Qb[bf][i][j], pc ? Lc + (int64_t)i * ldq + j : Lc, pc);
+  };
+
+  for (int ph = -3; ph <= 3 * (nt - 1) + 4; ++ph) {
+    const int m3 = ((ph % 3) + 3) % 3;
+    if (m3 == 0) {  // 1(k): column k+1 at step k, then its finalization
+      const int k = ph / 3;  // exact: ph is a multiple of 3
+      const int c = k + 1;
+      if (k >= nt || c >= Ecol) continue;
+      column(c, k, c < nt);
+    } else if (m3 == 2) {  // 2(k): column k+2 at step k
+      const int k = (ph - 2) / 3;
+      const int c = k + 2;
+      if (ph < 2 || k >= nt || c >= Ecol) continue;
+      column(c, k, false);
+    } else {  // 3(k): columns k+3 .. Ecol-1 at step k
+      const int k = (ph - 4) / 3;
+      if (ph < 4 || k >= nt || k + 3 >= Ecol) continue;
+      const long long lo = off(k + 3), hi = off(Ecol);
+      long long u = lo + ((bid - lo % G) % G + G) % G;
+      if (u >= hi) continue;
+      // Every tile of this phase reads column k only: wait once for all of it.
+      wait_flag_ge(p.colcnt + k, E - k);
+      int c = k + 3;
+      while (off(c + 1) <= u) ++c;
+      int r = c + (int)(u - off(c)), bf = 0;
+      issue(r, c, k, 0);
+      for (;;) {
+        const long long un = u + G;
+        int cn = c, rn = 0;
+        if (un < hi) {
+          while (off(cn + 1) <= un) ++cn;
+          rn = cn + (int)(un - off(cn));
+          issue(rn, cn, k, bf ^ 1);  // in flight during this update
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
         }
+        __syncthreads();
+        compute(r, c, bf);
+        __syncthreads();  // buffer bf is consumed
+        if (un >= hi) break;
+        u = un;
+        c = cn;
+        r = rn;
+        bf ^= 1;
       }
-      cp_async_commit();  // (an empty group for a slice keeps the group count in step)
-    };
-    __syncthreads();
-    if (tid == 0) s_next = atomicAdd(ctr, 1);
-    __syncthreads();
-    int t = s_next;
-    __syncthreads();
-    if (tid == 0) s_next = atomicAdd(ctr, 1);
-    __syncthreads();
-    int t1 = s_next, bf = 0;
-    bool have_lt = false;
-    if (t < nitems) issue(t, 0);
-    if (t1 < nitems) issue(t1, 1);
-    while (t < nitems) {
-      if (t1 < nitems)
-        cp_async_wait<1>();
-      else
-        cp_async_wait<0>();
-      __syncthreads();
-      int t2 = 0;
-      if (tid == 0) t2 = atomicAdd(ctr, 1);  // in flight during the item
-      int r, c;
-      decode(t, r, c);
-      if (t < nupd) {
-        const int rb = ext_rows(p, r), cb = ext_rows(p, c);
-        int64_t ldc;
-        double* C = ext_tile(p, r, c, ldc);
-        const int row = wm + gq;
-        if (wm < rb && wn < cb) {  // warp-uniform
-          double cold[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-          double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-#pragma unroll
-          for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const int col = wn + ni * 8 + 2 * tq + j;
-              if (row < rb && col < cb) cold[ni][j] = C[(int64_t)row * ldc + col];
-            }
-#pragma unroll
-          for (int ks = 0; ks < T; ks += 4) {
-            const double av = Pb[bf][row][ks + tq];
-            dmma_8x8x4(acc[0], av, Qb[bf][wn + gq][ks + tq]);
-            dmma_8x8x4(acc[1], av, Qb[bf][wn + 8 + gq][ks + tq]);
-          }
-#pragma unroll
-          for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const int col = wn + ni * 8 + 2 * tq + j;
-              if (row < rb && col < cb) C[(int64_t)row * ldc + col] = cold[ni][j] - acc[ni][j];
-            }
-        }
-      } else {
-        // Panel slice of tile (r, k+1), rows c .. c+sh-1.
-        const int rows = min(sh, ext_rows(p, r) - c);
-        if (rows > 0) {  // uniform over the CTA
-          if (!have_lt) wait_flag_ge(p.lflag, k + 1);
-          wait_flag_ge(p.colflag + r, k + 1);
-          int64_t ldx;
-          double* X = ext_tile(p, r, k + 1, ldx);
-          X += (int64_t)c * ldx;
-          for (int e = tid; e < T * T; e += blockDim.x) {
-            const int i = e / T, j = e % T;
-            if (!have_lt) Lt[i][j] = (i < tb1 && j <= i) ? p.D0[(int64_t)(o1 + i) * b + o1 + j] : 0.0;
-            if (i < sh) S[i][j] = (i < rows && j < tb1) ? X[(int64_t)i * ldx + j] : 0.0;
-          }
-          if (!have_lt && tid < T) rd[tid] = p.rdiag[((k + 1) & 1) * T + tid];
-          have_lt = true;
-          __syncthreads();
-          panel_solve(S, Lt, rd, rows, tb1);
-          for (int e = tid; e < rows * tb1; e += blockDim.x) {
-            const int i = e / tb1, j = e % tb1;
-            X[(int64_t)i * ldx + j] = S[i][j];
-          }
-        }
-      }
-      if (tid == 0) s_next = t2;
-      __syncthreads();  // the buffer is consumed, stores are done, s_next is published
-      if (t < ncol) raise_flag(p.colflag + r, k + 1);
-      t2 = s_next;
-      if (t2 < nitems) issue(t2, bf);
-      t = t1;
-      t1 = t2;
-      bf ^= 1;
     }
-    grid_barrier(p.bar, G, gen);
-  }
-  for (long long e = (long long)bid * blockDim.x + tid; e < (long long)p.b * p.b;
-       e += (long long)G * blockDim.x) {
-    const int i = (int)(e / p.b), j = (int)(e % p.b);
-    if (j > i) p.D0[(int64_t)i * b + j] = 0.0;
   }
 }
 
@@ -1122,24 +1047,22 @@ static double step_flops(double b, double a, int next, int schur) {
 
 cudaError_t factor_step_coop(double* D0, double* Lw, double* D1, double* Ar0, double* Ar1,
                              double* tip, int b, int a, int next, long long info_row0,
-                             void* scratch, cudaStream_t s, int schur) {
+                             void* scratch, cudaStream_t s, int schur, int64_t ld) {
   StepArgs p;
   p.D0 = D0; p.Lw = Lw; p.D1 = D1; p.Ar0 = Ar0; p.Ar1 = Ar1; p.tip = tip;
   p.b = b; p.a = a; p.nt = (b + T - 1) / T; p.na = (a + T - 1) / T; p.next = next ? 1 : 0;
+  p.ld = ld > 0 ? ld : b;
+  if (p.ld < b) return cudaErrorInvalidValue;
   p.schur = schur ? 1 : 0;
   p.row0 = info_row0;
-  p.bar = (CoopBar*)scratch;
-  p.rdiag = (double*)((char*)scratch + 256);
-  p.lflag = (int*)((char*)scratch + 1016);
-  p.smid0 = (int*)((char*)scratch + 1012);
-  p.ctr = (int*)((char*)scratch + 1024);
-  p.colflag = p.ctr + kStepMaxTiles;
+  p.pdone = (int*)scratch;
+  p.colcnt = p.pdone + kStepMaxExtTiles;
+  p.rdv = (double*)((char*)scratch + kStepFlagBytes);
   if (p.nt > kStepMaxTiles || 2 * p.nt + p.na > kStepMaxExtTiles) return cudaErrorInvalidValue;
   if (b < 1 || a < 0 || (next && !Lw) || (a > 0 && !Ar0) ||
       (schur && ((next && (!D1 || (a > 0 && !Ar1))) || (a > 0 && !tip))))
     return cudaErrorInvalidValue;
-  cudaError_t e =
-      cudaMemsetAsync(scratch, 0, 1024 + (kStepMaxTiles + kStepMaxExtTiles) * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, kStepFlagBytes, s);
   if (e != cudaSuccess) return e;
   const int G = step_grid();
   if (G < 2) return cudaErrorInvalidConfiguration;
@@ -1372,8 +1295,7 @@ __device__ __forceinline__ double trsv_tile_el(const double* L, int64_t ld, int 
 }
 
 __global__ void __launch_bounds__(256, 1) trsv_cluster_kernel(const double* L, int64_t ld, int nrow,
-                                                           const double* Dinv, double* x,
-                                                           int64_t ldx, int R, int trans) {
+                                                           double* x, int64_t ldx, int R, int trans) {
   __shared__ double Xk[T][65];
   __shared__ double Lk[T][T + 1];
   __shared__ double Ld[T][T + 1];
@@ -1409,35 +1331,7 @@ __global__ void __launch_bounds__(256, 1) trsv_cluster_kernel(const double* L, i
         }
       }
     }
-    if (owner && Dinv) {
-      // x_k = L_kk^{-1} r_k (or L_kk^{-T} r_k) with the precomputed tile inverse:
-      // independent dot products instead of a sequential substitution.
-      const double* D = Dinv + (int64_t)k * T * T;
-      for (int e = tid; e < T * T; e += blockDim.x) Ld[e / T][e % T] = D[e];
-      for (int e = tid; e < tb * R; e += blockDim.x)
-        Xk[e / R][e % R] = x[(int64_t)(o + e / R) * ldx + e % R];
-      __syncthreads();
-      for (int e = tid; e < tb * R; e += blockDim.x) {
-        const int i = e / R, q = e % R;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        if (!trans) {
-          for (int j = 0; j <= i; j += 4) {
-            a0 = fma(Ld[i][j], Xk[j][q], a0);
-            if (j + 1 <= i) a1 = fma(Ld[i][j + 1], Xk[j + 1][q], a1);
-            if (j + 2 <= i) a2 = fma(Ld[i][j + 2], Xk[j + 2][q], a2);
-            if (j + 3 <= i) a3 = fma(Ld[i][j + 3], Xk[j + 3][q], a3);
-          }
-        } else {
-          for (int j = i; j < tb; j += 4) {
-            a0 = fma(Ld[j][i], Xk[j][q], a0);
-            if (j + 1 < tb) a1 = fma(Ld[j + 1][i], Xk[j + 1][q], a1);
-            if (j + 2 < tb) a2 = fma(Ld[j + 2][i], Xk[j + 2][q], a2);
-            if (j + 3 < tb) a3 = fma(Ld[j + 3][i], Xk[j + 3][q], a3);
-          }
-        }
-        x[(int64_t)(o + i) * ldx + q] = (a0 + a1) + (a2 + a3);
-      }
-    } else if (owner) {
+    if (owner) {
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, c = e % T;
         Ld[i][c] = (i < tb && c <= i) ? L[(int64_t)(o + i) * ld + o + c] : 0.0;
@@ -1537,7 +1431,7 @@ static int trsv_cluster_size(cudaStream_t s) {
 }
 
 cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t ldx, int R,
-                       bool trans, cudaStream_t s, const double* Dinv) {
+                       bool trans, cudaStream_t s) {
   if (nrow <= 0) return cudaSuccess;
   if (R > 64) return cudaErrorInvalidValue;
   const int nt = (nrow + T - 1) / T;
@@ -1555,17 +1449,20 @@ cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, Dinv, x, ldx, R, trans ? 1 : 0);
+  return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, x, ldx, R, trans ? 1 : 0);
 }
 
-// x[M][R] += alpha * A[M][K] y[K][R]: one warp per row, lanes over k, fixed-order
-// shuffle reduction. R is processed 8 columns at a time.
+// out[M][R] = beta * xin + alpha * A[M][K] y[K][R]: one warp per row, lanes over
+// k, fixed-order shuffle reduction; R is processed 8 columns at a time. tri: A
+// is lower triangular (row r reads k <= r only). out may alias xin.
 __global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t lda, int M, int K,
                                                      const double* y, int64_t ldy, double* x,
-                                                     int64_t ldx, int R, double alpha) {
+                                                     int64_t ldx, int R, double alpha, double beta,
+                                                     const double* xin, int tri) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= M) return;
+  const int kend = tri ? min(K, row + 1) : K;
   for (int r0 = 0; r0 < R; r0 += 8) {
     const int rc = min(8, R - r0);
     double acc[8];
@@ -1576,9 +1473,9 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t ld
     for (int q = 0; q < 8; ++q) acc2[q] = 0.0;
     // Two k-steps per pass with separate sums: twice the loads in flight and
     // half the dependent chain; the two sums are added in a fixed order.
-    for (int k = lane; k < K; k += 64) {
+    for (int k = lane; k < kend; k += 64) {
       const double av = A[(int64_t)row * lda + k];
-      const bool two = k + 32 < K;
+      const bool two = k + 32 < kend;
       const double av2 = two ? A[(int64_t)row * lda + k + 32] : 0.0;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
@@ -1594,26 +1491,32 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t ld
       acc[q] = v;
     }
     if (lane == 0)
-      for (int q = 0; q < rc; ++q) x[(int64_t)row * ldx + r0 + q] += alpha * acc[q];
+      for (int q = 0; q < rc; ++q) {
+        const double base = beta == 0.0 ? 0.0 : beta * xin[(int64_t)row * ldx + r0 + q];
+        x[(int64_t)row * ldx + r0 + q] = base + alpha * acc[q];
+      }
   }
 }
 
-// x[M][R] += alpha * A^T y with A stored K x M: 32 rows per CTA (lane = row),
-// 8 warps split k and are summed in a fixed order.
+// out[M][R] = beta * xin + alpha * A^T y with A stored K x M: 32 rows per CTA
+// (lane = row), 8 warps split k and are summed in a fixed order. tri: A is lower
+// triangular (output row m reads k >= m only).
 __global__ void __launch_bounds__(256) gemv_t_kernel(const double* A, int64_t lda, int M, int K,
                                                      const double* y, int64_t ldy, double* x,
-                                                     int64_t ldx, int R, double alpha) {
+                                                     int64_t ldx, int R, double alpha, double beta,
+                                                     const double* xin, int tri) {
   __shared__ double red[8][32][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + lane;
   const int kchunk = (K + 7) / 8, kb = w * kchunk, ke = min(K, kb + kchunk);
+  const int kb_row = tri ? max(kb, row) : kb;
   for (int r0 = 0; r0 < R; r0 += 8) {
     const int rc = min(8, R - r0);
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
     if (row < M)
-      for (int k = kb; k < ke; ++k) {
+      for (int k = kb_row; k < ke; ++k) {
         const double av = A[(int64_t)k * lda + row];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -1626,35 +1529,41 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const double* A, int64_t ld
       for (int q = 0; q < rc; ++q) {
         double v = 0.0;
         for (int ww = 0; ww < 8; ++ww) v += red[ww][lane][q];
-        x[(int64_t)row * ldx + r0 + q] += alpha * v;
+        const double base = beta == 0.0 ? 0.0 : beta * xin[(int64_t)row * ldx + r0 + q];
+        x[(int64_t)row * ldx + r0 + q] = base + alpha * v;
       }
     }
     __syncthreads();
   }
 }
 
-// x[M][R] += alpha * A^T y (A stored K x M), R <= 8: a cluster of kGemvSplit
-// CTAs per 32 output rows splits k; in each CTA 8 warps split its k-range
-// (lane = row), the warps' sums are added in a fixed order in shared memory, and
-// rank 0 adds the CTAs' sums in rank order from distributed shared memory.
+// out[M][R] = beta * xin + alpha * A^T y (A stored K x M), R <= 8: a cluster of
+// kGemvSplit CTAs per 32 output rows splits k; in each CTA 8 warps split its
+// k-range (lane = row), the warps' sums are added in a fixed order in shared
+// memory, and rank 0 adds the CTAs' sums in rank order from distributed shared
+// memory. tri: A is lower triangular (output row m reads k >= m only).
 constexpr int kGemvSplit = 4;
 
 __global__ void __launch_bounds__(256) gemv_t_split_kernel(const double* A, int64_t lda, int M, int K,
                                                           const double* y, int64_t ldy, double* x,
-                                                          int64_t ldx, int R, double alpha) {
+                                                          int64_t ldx, int R, double alpha, double beta,
+                                                          const double* xin, int tri) {
   __shared__ double red[8][32][8];
   __shared__ double part_sum[32][8];
   unsigned part;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(part));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = (blockIdx.x / kGemvSplit) * 32 + lane;
-  const int kq = (K + kGemvSplit - 1) / kGemvSplit, kp0 = (int)part * kq, kp1 = min(K, kp0 + kq);
+  // Under a triangular A the k-range of this group of 32 rows starts at its first row.
+  const int k0 = tri ? min(K, (blockIdx.x / kGemvSplit) * 32) : 0;
+  const int kq = (K - k0 + kGemvSplit - 1) / kGemvSplit, kp0 = k0 + (int)part * kq, kp1 = min(K, kp0 + kq);
   const int kchunk = (kp1 - kp0 + 7) / 8, kb = kp0 + w * kchunk, ke = min(kp1, kb + kchunk);
+  const int kb_row = tri ? max(kb, row) : kb;
   double acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
   if (row < M)
-    for (int k = kb; k < ke; ++k) {
+    for (int k = kb_row; k < ke; ++k) {
       const double av = A[(int64_t)k * lda + row];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
@@ -1676,18 +1585,22 @@ __global__ void __launch_bounds__(256) gemv_t_split_kernel(const double* A, int6
     for (int q = 0; q < R; ++q) {
       double v = part_sum[lane][q];
       for (unsigned p = 1; p < kGemvSplit; ++p) v += ld_dsmem(&part_sum[lane][q], p);
-      x[(int64_t)row * ldx + q] += alpha * v;
+      const double base = beta == 0.0 ? 0.0 : beta * xin[(int64_t)row * ldx + q];
+      x[(int64_t)row * ldx + q] = base + alpha * v;
     }
   }
   cluster_sync_all();  // the partial sums stay readable until rank 0 is done
 }
 
 cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K, const double* y,
-                       int64_t ldy, double* x, int64_t ldx, int R, double alpha, cudaStream_t s) {
-  if (M <= 0 || K <= 0 || R <= 0) return cudaSuccess;
-  TimedLaunch tl(K_GEMV, 2.0 * M * K * R, s);
+                       int64_t ldy, double* x, int64_t ldx, int R, double alpha, cudaStream_t s,
+                       double beta, const double* xin, int triA) {
+  if (M <= 0 || R <= 0) return cudaSuccess;
+  if (!xin) xin = x;
+  const int tri = triA == TRI_LOWER ? 1 : 0;
+  TimedLaunch tl(K_GEMV, 2.0 * M * K * R * (tri ? 0.5 : 1.0), s);
   if (opA == OP_N) {
-    gemv_n_kernel<<<ceil_div(M, 8), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
+    gemv_n_kernel<<<ceil_div(M, 8), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
     return cudaGetLastError();
   }
   if (R <= 8 && K >= 8 * kGemvSplit) {
@@ -1702,9 +1615,10 @@ cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, gemv_t_split_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha);
+    return cudaLaunchKernelEx(&cfg, gemv_t_split_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha, beta,
+                              xin, tri);
   }
-  gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha);
+  gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
   return cudaGetLastError();
 }
 

@@ -600,8 +600,9 @@ __device__ __forceinline__ int part_of(const SplitOp& op, int k) {
 // slab and merges with atomicMax (FP64 bit patterns order |x|).
 __global__ void __launch_bounds__(256) split_rowmax_kernel(SplitOp sa_op, SplitOp sb_op,
                                                            unsigned long long* rmA,
-                                                           unsigned long long* rmB) {
-  const int side = blockIdx.z & 1, zl = blockIdx.z >> 1;
+                                                           unsigned long long* rmB, int nsides) {
+  const int side = nsides == 2 ? (int)(blockIdx.z & 1) : 0;
+  const int zl = nsides == 2 ? (int)(blockIdx.z >> 1) : (int)blockIdx.z;
   const SplitOp& op = side == 0 ? sa_op : sb_op;
   unsigned long long* rm = side == 0 ? rmA : rmB;
   const SplitArgs& a0 = op.part[0];
@@ -648,13 +649,15 @@ __global__ void __launch_bounds__(256) split_rowmax_kernel(SplitOp sa_op, SplitO
 }
 
 // Slices of one 32 x 32 tile of the concatenated operand (blockIdx.z = 2 * batch
-// entry + side), plus the row scales (first column of tiles) and, for side A, the
-// zeroing of the int64 accumulator rows.
+// entry + side, or the batch entry when only side A is split), plus the row
+// scales (first column of tiles) and, for side A, the zeroing of the int64
+// accumulator rows.
 __global__ void __launch_bounds__(256) split_digits_kernel(SplitOp sa_op, SplitOp sb_op,
                                                            const unsigned long long* rmA,
                                                            const unsigned long long* rmB,
-                                                           long long* T, int Tcols) {
-  const int side = blockIdx.z & 1, zl = blockIdx.z >> 1;
+                                                           long long* T, int Tcols, int nsides) {
+  const int side = nsides == 2 ? (int)(blockIdx.z & 1) : 0;
+  const int zl = nsides == 2 ? (int)(blockIdx.z >> 1) : (int)blockIdx.z;
   const SplitOp& op = side == 0 ? sa_op : sb_op;
   const unsigned long long* rm = side == 0 ? rmA : rmB;
   const SplitArgs& a0 = op.part[0];
@@ -838,7 +841,13 @@ static void fill_op(SplitOp* op, const Part* parts, int np, int nb1, int zbase, 
 // count, per device; -1 if a query failed.
 static PerDevice g_tc_dyn_limit, g_tc_sms;
 
-cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
+static bool same_part(const Part& x, const Part& y) {
+  return x.X == y.X && x.sr == y.sr && x.sk == y.sk && x.s1 == y.s1 && x.s2 == y.s2 && x.K == y.K &&
+         x.mask == y.mask;
+}
+
+cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s,
+                    bool reuse_b) {
   if (g.nterms < 1 || g.nterms > kMaxTerms) return cudaErrorInvalidValue;
   // Several terms are one product over the concatenated k range when they share
   // alpha and no operand is triangular; otherwise they run one after the other.
@@ -851,7 +860,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
       gi.t[0] = g.t[i];
       gi.nterms = 1;
       if (i > 0) gi.beta = 1.0;
-      cudaError_t e = gemm_tc(gi, mode, ws, ws_bytes, s);
+      cudaError_t e = gemm_tc(gi, mode, ws, ws_bytes, s, false);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -877,11 +886,17 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
   if (Kp > 16384) return cudaErrorInvalidValue;  // int64 accumulator headroom
   const int Mp = (int)rup(M, BM), Np = (int)rup(N, BN);
   const int total = g.nb1 * g.nb2;
+  // A product of an operand with its own transpose (a SYRK, L^-T L^-1) splits it
+  // once: op(B)^T has the rows, scales and slices of op(A).
+  const bool self = g.nterms == 1 && M == N && Mp == Np && same_part(pa[0], pb[0]);
   // Batch entries per pass: as many as the design size and the workspace allow.
   int chunk_nb = tc_batch_chunk(M, N, Kp);
   if (chunk_nb > total) chunk_nb = total;
   while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) --chunk_nb;
   if (tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
+  // The caller's previous call left this call's op(B) split in the workspace:
+  // only valid for one chunk holding the whole batch.
+  if (reuse_b && chunk_nb != total) reuse_b = false;
   const long long dyn_limit = per_device(g_tc_dyn_limit, []() -> long long {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa;
@@ -947,20 +962,22 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     cudaError_t e;
     {
       TimedLaunch tl(K_TC_SPLIT, 0.0, s);
-      const int bands = (Mp > Np ? Mp : Np) / 32;
+      const int nsides = (self || reuse_b) ? 1 : 2;
+      const int bands = (nsides == 1 ? Mp : (Mp > Np ? Mp : Np)) / 32;
       if (mode == TC_OZ) {
-        e = cudaMemsetAsync(rmA, 0, ((size_t)Mp + Np) * nb * 8, s);
+        e = cudaMemsetAsync(rmA, 0, ((size_t)Mp + (nsides == 2 ? Np : 0)) * nb * 8, s);
         if (e != cudaSuccess) return e;
-        split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, 2 * nb), 256, 0, s>>>(opA, opB, rmA, rmB);
+        split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, nsides * nb), 256, 0, s>>>(opA, opB, rmA, rmB,
+                                                                                      nsides);
       }
-      split_digits_kernel<<<dim3(Kp / 32, bands, 2 * nb), 256, 0, s>>>(
-          opA, opB, rmA, rmB, (mode == TC_OZ && chunks > 1) ? Tacc : nullptr, Np);
+      split_digits_kernel<<<dim3(Kp / 32, bands, nsides * nb), 256, 0, s>>>(
+          opA, opB, rmA, rmB, (mode == TC_OZ && chunks > 1) ? Tacc : nullptr, Np, nsides);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, (uint64_t)nb * S, (uint64_t)Mp, (uint64_t)Kp, BM, S) ||
-        !make_map(&mB, Bs, (uint64_t)nb * S, (uint64_t)Np, (uint64_t)Kp, BN, S))
+        !make_map(&mB, self ? As : Bs, (uint64_t)nb * S, (uint64_t)(self ? Mp : Np), (uint64_t)Kp, BN, S))
       return cudaErrorInvalidValue;
     TcArgs a{};
     a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.ups = ups; a.chunks = chunks;
@@ -969,7 +986,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     a.Mpad = Mp; a.Npad = Np; a.nstages = nstages; a.lowerC = g.lowerC;
     a.triA = g.nterms == 1 ? t0.triA : TRI_NONE;
     a.triB = g.nterms == 1 ? t0.triB : TRI_NONE;
-    a.sa = sa; a.sb = sb;
+    a.sa = sa; a.sb = self ? sa : sb;
     a.co = COut{g.C, g.ldc, g.sC1, g.sC2, g.nb1, c0};
     a.alpha = t0.alpha; a.beta = g.beta;
     const long long grid = std::min<long long>(a.items, sms);
@@ -985,7 +1002,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
       const int64_t elems = (int64_t)M * N;
       TimedLaunch tl(K_TC_FINAL, 0.0, s);
       tc_finalize_kernel<<<dim3((unsigned)((elems + 255) / 256), nb), 256, 0, s>>>(
-          Tacc, M, N, Mp, Np, sa, sb, a.co, t0.alpha, g.beta, g.lowerC);
+          Tacc, M, N, Mp, Np, a.sa, a.sb, a.co, t0.alpha, g.beta, g.lowerC);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -13,8 +13,12 @@ constexpr int kOzSlices = 7;     // BF16 digit slices per FP64 operand (7 bits e
 int tc_slices(int mode);
 // Scratch bytes for one call of gemm_tc with these sizes and batch (K <= 16384).
 size_t tc_workspace_bytes(int mode, int M, int N, int K, int batch);
-// Single-term GEMM (g.nterms == 1) on the tensor cores; ws: >= tc_workspace_bytes.
-cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s);
+// GEMM on the tensor cores; ws: >= tc_workspace_bytes. Terms that share alpha
+// and have no triangular operand run as one product over the concatenated k.
+// reuse_b: op(B) is the one the previous call on this workspace split (same
+// parts, sizes and batch, the data unchanged since), so it is not split again.
+cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s,
+                    bool reuse_b = false);
 // Reads and clears the bounded-wait timeout flag of the tensor-core kernels.
 cudaError_t tc_error_read_reset(int* out);
 

@@ -1,6 +1,8 @@
 """bta_factor_selinv_host / bta_factor_selinv_all: the whole per-matrix sequence
-in one call (from host memory with the copies overlapped, or on device buffers),
-the solve overlapped with the selected inversion's prologue.
+in one call (from host memory with the copies overlapped, or on device buffers).
+The solve there uses the block inverses L_ii^{-1} of the selected inversion's
+prologue and runs beside the rest of it, so its result agrees with bta_solve's
+(substitution) to rounding, while X and log det are bit-identical.
 
 Checked against the oracle (X on the pattern, log det, solve) and against the
 device-buffer entry points, over the fused FP64 step (b >= 128), the small-b
@@ -80,7 +82,7 @@ def test_device_all_in_one_matches_separate_calls(n, b, a, nrhs):
     assert abs(float(ld.item()) - ldo) <= TOL * max(1.0, abs(ldo))
     if nrhs:
         assert rel_fro(host(R), oracle.solve(F, r)) <= TOL
-    # bit-identical to the four separate calls
+    # X and log det bit-identical to the four separate calls; the solution to rounding
     D2, L2, A2, T2 = dev(d), dev(l), dev(ar), dev(t)
     bta.factor(D2, L2, A2, T2)
     ld2 = bta.logdet(D2, T2)
@@ -93,4 +95,4 @@ def test_device_all_in_one_matches_separate_calls(n, b, a, nrhs):
         assert torch.equal(x1, x2)
     assert float(ld.item()) == float(ld2.item())
     if nrhs:
-        assert torch.equal(R, R2)
+        assert rel_fro(host(R), host(R2)) <= 1e-13

@@ -110,3 +110,23 @@ def test_bf16x3_mixed_error_is_bounded():
     bound = 4 * 4.0 * 2.0 ** -16
     assert worst_block_error(Lg, (F.diag, F.lower, F.arrow, F.tip)) <= bound
     assert worst_block_error([host(x) for x in (D, Lo, Ar, Ti)], oracle.pobtasi(F)) <= bound
+
+
+def test_gemm_ozaki_self_product_after_another_call():
+    """A A^T splits A once: op(B)^T has the same rows, scales and slices. With
+    fewer output tiles than SMs (1024 x 1024: 128 tiles) the k-units of a tile are
+    split over CTAs and a finalize kernel applies the scales. A previous call with
+    very different scales must leave nothing behind that this product reads."""
+    rng = np.random.default_rng(5)
+    B0 = rng.standard_normal((1024, 1024)) * 1e6
+    bta.gemm(dev(B0), dev(B0.T.copy()), precision="ozaki")
+    torch.cuda.synchronize()
+    s = 2.0 ** rng.integers(-20, 21, 1024).astype(np.float64)
+    An = rng.standard_normal((1024, 1024))
+    A = An * s[:, None]
+    got = host(bta.gemm(dev(A), dev(A), trans_b=True, precision="ozaki"))
+    torch.cuda.synchronize()
+    assert bta.tc_status() == 0
+    # compare on the unscaled rows: C_ij / (s_i s_j) against An An^T
+    err = rel_fro(got / np.outer(s, s), An @ An.T)
+    assert err <= 1e-12, err
