@@ -167,8 +167,12 @@ cudaError_t gemm_run(const GemmArgs& g, int cls, const TcWs& tw, int prec, cudaS
   }
   // The tensor-core path costs three launches and a splitting pass; it pays for
   // products of at least 2^25 multiply-adds (a 512^3 block product).
+  // A product with few rows (the arrowhead's a) pays for the tensor cores only
+  // when the split of its large op(B) is already in the workspace.
   const double macs = (double)g.M * g.N * ksum * g.nb1 * g.nb2;
-  if (g.M >= 64 && g.N >= 64 && kmax >= 64 && macs >= 33554432.0) {
+  const bool large = g.M >= 64 && macs >= 33554432.0;
+  const bool skinny_reuse = reuse_b && g.nb1 * g.nb2 == 1;
+  if (g.N >= 64 && kmax >= 64 && (large || skinny_reuse)) {
     if (used_tc) *used_tc = true;
     return gemm_tc(g, tc_mode_of(prec), tw.p, tw.bytes, s, reuse_b);
   }
@@ -194,7 +198,10 @@ constexpr int64_t kCoopMinB = 128;
 // run in FP64 anyway (BF16x3; n=256, b=2048: 3.45 s against 4.66 s); with Ozaki
 // they take the inverse + tensor-core product, whose cost grows slower than the
 // FP64 solve's b^3 (n=256, b=2048: 2.07 s against 3.64 s).
-constexpr int64_t kHybridMaxB = 1024;
+#ifndef BTA_HYBRID_MAX_B
+#define BTA_HYBRID_MAX_B 1024
+#endif
+constexpr int64_t kHybridMaxB = BTA_HYBRID_MAX_B;
 
 // L_ii = POTRF(A_ii) and Linv = L_ii^{-1} (row stride b) for a block whose
 // triangular solves go to the tensor cores (Ozaki, b > kHybridMaxB), by halves
@@ -268,13 +275,15 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       double* Ai = a > 0 ? arrow + i * a * b : nullptr;
       BTA_TRY(factor_step_coop(Di, Li, nullptr, Ai, nullptr, nullptr, B, Aa, nx ? 1 : 0, i * b,
                                w.coop, s, /*schur=*/0));
+      bool split_L = false;  // the SYRK's split of L_{i+1,i} is in the workspace
       if (nx)  // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
         BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
-                                  Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s));
+                                  Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s, &split_L));
       if (a > 0) {
         if (nx)  // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
           BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
-                                    Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
+                                    Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s, nullptr,
+                           split_L));
         // A_{n,n} -= L_{n,i} L_{n,i}^T
         BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
                                   tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, prec, s));
@@ -297,32 +306,31 @@ int factor_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
         BTA_TRY(potrf_blocks(Di, b, bb, 1, B, i * b, 0, s));
       BTA_TRY(trtri_blocks(Di, b, bb, w.Linv, b, bb, 1, B, s, trtri_hook, &hc));
     }
-    if (i + 1 < n) {
-      double* Li = lower + i * bb;
-      // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
+    // The two TRSMs share op(B) = L_ii^{-T}, and the arrow's Schur product shares
+    // the SYRK's L_{i+1,i}: on the tensor cores each pair splits it once.
+    double* Li = i + 1 < n ? lower + i * bb : nullptr;
+    double* Ai = a > 0 ? arrow + i * a * b : nullptr;
+    bool split_inv = false, split_L = false;
+    if (Li)  // L_{i+1,i} = A_{i+1,i} L_ii^{-T}
       BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.W, b, B, B, 0.0, 0), CLS_TRSM, tw, prec, s));
+                                w.W, b, B, B, 0.0, 0), CLS_TRSM, tw, prec, s, &split_inv));
+    if (Ai) {  // L_{n,i} = A_{n,i} L_ii^{-T}
+      BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
+                                w.Wa, b, Aa, B, 0.0, 0), CLS_TRSM, tw, prec, s, nullptr, split_inv));
+      BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    if (Li) {
       BTA_TRY(cudaMemcpyAsync(Li, w.W, bb * sizeof(double), cudaMemcpyDeviceToDevice, s));
       // A_{i+1,i+1} -= L_{i+1,i} L_{i+1,i}^T  (lower tiles)
       BTA_TRY(gemm_run(one_term(term(Li, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
-                                Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s));
+                                Di + bb, b, B, B, 1.0, 1), CLS_SCHUR, tw, prec, s, &split_L));
+      if (Ai)  // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
+        BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Li, b, OP_T, TRI_NONE, B, -1.0),
+                                  Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s, nullptr, split_L));
     }
-    if (a > 0) {
-      double* Ai = arrow + i * a * b;
-      // L_{n,i} = A_{n,i} L_ii^{-T}
-      BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, w.Linv, b, OP_T, TRI_UPPER, B, 1.0),
-                                w.Wa, b, Aa, B, 0.0, 0), CLS_TRSM, tw, prec, s));
-      BTA_TRY(cudaMemcpyAsync(Ai, w.Wa, a * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      if (i + 1 < n) {
-        // A_{n,i+1} -= L_{n,i} L_{i+1,i}^T
-        BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, lower + i * bb, b, OP_T, TRI_NONE,
-                                       B, -1.0),
-                                  Ai + a * b, b, Aa, B, 1.0, 0), CLS_SCHUR, tw, prec, s));
-      }
-      // A_{n,n} -= L_{n,i} L_{n,i}^T
+    if (Ai)  // A_{n,n} -= L_{n,i} L_{n,i}^T
       BTA_TRY(gemm_run(one_term(term(Ai, b, OP_N, TRI_NONE, Ai, b, OP_T, TRI_NONE, B, -1.0),
                                 tip, a, Aa, Aa, 1.0, 1), CLS_SCHUR, tw, prec, s));
-    }
   }
   if (a > 0) BTA_TRY(potrf_blocks(tip, a, a * a, 1, Aa, n * b, 0, s));
   return 0;
@@ -396,16 +404,16 @@ int selinv_impl(int64_t n, int64_t b, int64_t a, double* diag, double* lower, do
       BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, &b_split));
     }
     if (a > 0) {
-      // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i
+      // X_{n,i} = -X_{n,i+1} G_i - X_nn H_i (terms in the order of op(B) = [G_i; H_i],
+      // whose split it reuses on the tensor cores)
       GemmArgs g = one_term(term(tip, a, OP_N, TRI_NONE, Hi, b, OP_N, TRI_NONE, Aa, -1.0),
                             arrow + i * ab, b, Aa, B, 0.0, 0);
       if (i + 1 < n) {
-        g.t[1] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
+        g.t[1] = g.t[0];
+        g.t[0] = term(arrow + (i + 1) * ab, b, OP_N, TRI_NONE, Gi, b, OP_N, TRI_NONE, B, -1.0);
         g.nterms = 2;
       }
-      bool tc = false;
-      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, &tc));
-      if (tc) b_split = false;  // that product used the workspace too
+      BTA_TRY(gemm_run(g, CLS_SELINV, tw, prec, s, nullptr, b_split));
     }
     // X_ii = M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i  (lower tiles, then mirrored)
     GemmArgs g{};

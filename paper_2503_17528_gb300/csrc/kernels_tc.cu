@@ -790,13 +790,17 @@ static inline int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int tc_slices(int mode) { return mode == TC_X3 ? 2 : kOzSlices; }
 
 // Bytes of scratch one chunk of `nb` batch entries needs (k extent K).
+// Workspace of one chunk, in this order: op(B)'s slices, scales and row maxima
+// (at offsets that depend on N, K and the batch only, so that a later call with
+// another M can reuse them), then op(A)'s, then the int64 accumulators.
+static size_t tc_side_bytes(int64_t rows_pad, int64_t Kp, int64_t s, int64_t nb) {
+  return rup(rows_pad * Kp * s * 2 * nb, 256) + 2 * rup(rows_pad * 8 * nb, 256);
+}
+
 static size_t tc_chunk_bytes(int mode, int M, int N, int K, int nb) {
   const int64_t s = tc_slices(mode);
   const int64_t Mp = rup(M, BM), Np = rup(N, BN), Kp = rup(K, BK);
-  size_t b = 0;
-  b += rup((Mp + Np) * Kp * s * 2 * nb, 256);  // slices
-  b += rup((Mp + Np) * 8 * nb, 256);           // scales
-  b += rup((Mp + Np) * 8 * nb, 256);           // row maxima
+  size_t b = tc_side_bytes(Np, Kp, s, nb) + tc_side_bytes(Mp, Kp, s, nb);
   if (mode == TC_OZ) b += rup(Mp * Np * 8 * nb, 256);  // int64 accumulators (split tiles)
   return b;
 }
@@ -894,9 +898,10 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
   if (chunk_nb > total) chunk_nb = total;
   while (chunk_nb > 1 && tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) --chunk_nb;
   if (tc_chunk_bytes(mode, M, N, Kp, chunk_nb) > ws_bytes) return cudaErrorInvalidValue;
-  // The caller's previous call left this call's op(B) split in the workspace:
-  // only valid for one chunk holding the whole batch.
-  if (reuse_b && chunk_nb != total) reuse_b = false;
+  // The caller's previous call left this call's op(B) split in the workspace
+  // (op(B)'s part of it sits at the start whatever M is): only valid for one
+  // chunk holding the whole batch.
+  if (reuse_b && (chunk_nb != total || self)) reuse_b = false;
   const long long dyn_limit = per_device(g_tc_dyn_limit, []() -> long long {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa;
@@ -946,16 +951,26 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     const int ups = (nunits + chunks - 1) / chunks;
     chunks = (nunits + ups - 1) / ups;
     char* w = (char*)ws;
+    __nv_bfloat16* Bs = (__nv_bfloat16*)w;
+    w += rup((int64_t)Np * Kp * S * 2 * nb, 256);
+    double* sb = (double*)w;
+    w += rup((int64_t)Np * 8 * nb, 256);
+    unsigned long long* rmB = (unsigned long long*)w;
+    w += rup((int64_t)Np * 8 * nb, 256);
     __nv_bfloat16* As = (__nv_bfloat16*)w;
-    __nv_bfloat16* Bs = As + (int64_t)nb * S * Mp * Kp;
-    w += rup(((int64_t)Mp + Np) * Kp * S * 2 * nb, 256);
+    w += rup((int64_t)Mp * Kp * S * 2 * nb, 256);
     double* sa = (double*)w;
-    double* sb = sa + (int64_t)nb * Mp;
-    w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
+    w += rup((int64_t)Mp * 8 * nb, 256);
     unsigned long long* rmA = (unsigned long long*)w;
-    unsigned long long* rmB = rmA + (int64_t)nb * Mp;
-    w += rup(((int64_t)Mp + Np) * 8 * nb, 256);
+    w += rup((int64_t)Mp * 8 * nb, 256);
     long long* Tacc = (long long*)w;
+    // A self-product splits its operand once, into op(B)'s place, and reads op(A)
+    // from there too.
+    if (self) {
+      As = Bs;
+      sa = sb;
+      rmA = rmB;
+    }
     SplitOp opA, opB;
     fill_op(&opA, pa, g.nterms, g.nb1, c0, M, Kp, Mp, S, mode, nb, As, sa);
     fill_op(&opB, pb, g.nterms, g.nb1, c0, N, Kp, Np, S, mode, nb, Bs, sb);
@@ -965,7 +980,8 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
       const int nsides = (self || reuse_b) ? 1 : 2;
       const int bands = (nsides == 1 ? Mp : (Mp > Np ? Mp : Np)) / 32;
       if (mode == TC_OZ) {
-        e = cudaMemsetAsync(rmA, 0, ((size_t)Mp + (nsides == 2 ? Np : 0)) * nb * 8, s);
+        e = cudaMemsetAsync(rmA, 0, (size_t)Mp * nb * 8, s);
+        if (e == cudaSuccess && nsides == 2) e = cudaMemsetAsync(rmB, 0, (size_t)Np * nb * 8, s);
         if (e != cudaSuccess) return e;
         split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, nsides * nb), 256, 0, s>>>(opA, opB, rmA, rmB,
                                                                                       nsides);
@@ -977,7 +993,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     }
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, (uint64_t)nb * S, (uint64_t)Mp, (uint64_t)Kp, BM, S) ||
-        !make_map(&mB, self ? As : Bs, (uint64_t)nb * S, (uint64_t)(self ? Mp : Np), (uint64_t)Kp, BN, S))
+        !make_map(&mB, Bs, (uint64_t)nb * S, (uint64_t)Np, (uint64_t)Kp, BN, S))
       return cudaErrorInvalidValue;
     TcArgs a{};
     a.M = M; a.N = N; a.Kc = Kp; a.unitk = unitk; a.nunits = nunits; a.ups = ups; a.chunks = chunks;
@@ -986,7 +1002,7 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
     a.Mpad = Mp; a.Npad = Np; a.nstages = nstages; a.lowerC = g.lowerC;
     a.triA = g.nterms == 1 ? t0.triA : TRI_NONE;
     a.triB = g.nterms == 1 ? t0.triB : TRI_NONE;
-    a.sa = sa; a.sb = self ? sa : sb;
+    a.sa = sa; a.sb = sb;
     a.co = COut{g.C, g.ldc, g.sC1, g.sC2, g.nb1, c0};
     a.alpha = t0.alpha; a.beta = g.beta;
     const long long grid = std::min<long long>(a.items, sms);

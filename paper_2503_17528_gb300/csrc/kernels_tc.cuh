@@ -16,7 +16,9 @@ size_t tc_workspace_bytes(int mode, int M, int N, int K, int batch);
 // GEMM on the tensor cores; ws: >= tc_workspace_bytes. Terms that share alpha
 // and have no triangular operand run as one product over the concatenated k.
 // reuse_b: op(B) is the one the previous call on this workspace split (same
-// parts, sizes and batch, the data unchanged since), so it is not split again.
+// parts, N, k extent and batch, the data unchanged since; M may differ), so it
+// is not split again. A self-product (op(B)^T is op(A)) leaves its operand's
+// split in op(B)'s place, where a following product with that op(B) can reuse it.
 cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cudaStream_t s,
                     bool reuse_b = false);
 // Reads and clears the bounded-wait timeout flag of the tensor-core kernels.
