@@ -1452,6 +1452,13 @@ cudaError_t trsv_lower(const double* L, int64_t ld, int nrow, double* x, int64_t
   return cudaLaunchKernelEx(&cfg, trsv_cluster_kernel, L, ld, nrow, x, ldx, R, trans ? 1 : 0);
 }
 
+// Waits until the grid this launch depends on has completed and its writes are
+// visible (programmatic dependent launch: the launch itself and the scheduling
+// of its CTAs overlap the previous kernel's drain). A no-op for a normal launch.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // out[M][R] = beta * xin + alpha * A[M][K] y[K][R]: one warp per row, lanes over
 // k, fixed-order shuffle reduction; R is processed 8 columns at a time. tri: A
 // is lower triangular (row r reads k <= r only). out may alias xin.
@@ -1459,6 +1466,7 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const double* A, int64_t ld
                                                      const double* y, int64_t ldy, double* x,
                                                      int64_t ldx, int R, double alpha, double beta,
                                                      const double* xin, int tri) {
+  grid_dependency_wait();
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= M) return;
@@ -1505,6 +1513,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(const double* A, int64_t ld
                                                      const double* y, int64_t ldy, double* x,
                                                      int64_t ldx, int R, double alpha, double beta,
                                                      const double* xin, int tri) {
+  grid_dependency_wait();
   __shared__ double red[8][32][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + lane;
@@ -1548,6 +1557,7 @@ __global__ void __launch_bounds__(256) gemv_t_split_kernel(const double* A, int6
                                                           const double* y, int64_t ldy, double* x,
                                                           int64_t ldx, int R, double alpha, double beta,
                                                           const double* xin, int tri) {
+  grid_dependency_wait();
   __shared__ double red[8][32][8];
   __shared__ double part_sum[32][8];
   unsigned part;
@@ -1599,27 +1609,32 @@ cudaError_t gemv_multi(const double* A, int64_t lda, int opA, int M, int K, cons
   if (!xin) xin = x;
   const int tri = triA == TRI_LOWER ? 1 : 0;
   TimedLaunch tl(K_GEMV, 2.0 * M * K * R * (tri ? 0.5 : 1.0), s);
+  // Programmatic dependent launch: consecutive products of a solve overlap
+  // launch latency; each kernel waits for its predecessor before reading.
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (opA == OP_N) {
-    gemv_n_kernel<<<ceil_div(M, 8), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
-    return cudaGetLastError();
+    cfg.gridDim = dim3(ceil_div(M, 8));
+    return cudaLaunchKernelEx(&cfg, gemv_n_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
   }
   if (R <= 8 && K >= 8 * kGemvSplit) {
-    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ceil_div(M, 32) * kGemvSplit);
-    cfg.blockDim = dim3(256);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kGemvSplit;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = kGemvSplit;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, gemv_t_split_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha, beta,
                               xin, tri);
   }
-  gemv_t_kernel<<<ceil_div(M, 32), 256, 0, s>>>(A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
-  return cudaGetLastError();
+  cfg.gridDim = dim3(ceil_div(M, 32));
+  return cudaLaunchKernelEx(&cfg, gemv_t_kernel, A, lda, M, K, y, ldy, x, ldx, R, alpha, beta, xin, tri);
 }
 
 int arrow_chunks(int64_t n) { return (int)(n < 256 ? n : 256); }

@@ -580,12 +580,14 @@ __device__ __forceinline__ void oz_digits(double x, unsigned long long mb, int s
     if (bits < 0) Y = -Y;
   }
   // Balanced base-128 digits, least significant first: d_s ... d_2 in [-64, 63], d_1 the rest.
+  // (the digits fit in 32 bits: converting from int keeps the 64-bit integer
+  // conversion, which issues on this part's narrow FP64 pipe, out of the loop)
   for (int p = s - 1; p >= 1; --p) {
     const long long d = ((Y + 64) & 127) - 64;
-    dig[p] = (float)d;
+    dig[p] = (float)(int)d;
     Y = (Y - d) >> 7;
   }
-  dig[0] = (float)Y;
+  dig[0] = (float)(int)Y;
 }
 
 // Part of `op` holding concatenated column k (parts start on 32-column boundaries).
@@ -596,8 +598,9 @@ __device__ __forceinline__ int part_of(const SplitOp& op, int k) {
 }
 
 // Row maxima of |x| over the concatenated k range, both operands in one launch:
-// blockIdx.z = 2 * batch entry + side; each CTA reduces 32 rows over a 256-wide
-// slab and merges with atomicMax (FP64 bit patterns order |x|).
+// blockIdx.z = 2 * batch entry + side; each CTA reduces 32 rows over a
+// kRowmaxSlab-wide slab and merges with atomicMax (FP64 bit patterns order |x|).
+constexpr int kRowmaxSlab = 64;
 __global__ void __launch_bounds__(256) split_rowmax_kernel(SplitOp sa_op, SplitOp sb_op,
                                                            unsigned long long* rmA,
                                                            unsigned long long* rmB, int nsides) {
@@ -606,14 +609,14 @@ __global__ void __launch_bounds__(256) split_rowmax_kernel(SplitOp sa_op, SplitO
   const SplitOp& op = side == 0 ? sa_op : sb_op;
   unsigned long long* rm = side == 0 ? rmA : rmB;
   const SplitArgs& a0 = op.part[0];
-  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 256;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * kRowmaxSlab;
   if (r0 >= a0.Rpad || k0 >= a0.Kp) return;
   __shared__ unsigned long long red[8][32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   unsigned long long m = 0;
   for (int pi = 0; pi < op.nparts; ++pi) {
     const SplitArgs& a = op.part[pi];
-    const int lo = max(k0, a.kout0), hi = min(k0 + 256, a.kout0 + a.Kc);
+    const int lo = max(k0, a.kout0), hi = min(k0 + kRowmaxSlab, a.kout0 + a.Kc);
     if (lo >= hi) continue;
     const double* X = part_base(a, zl);
     if (a.sk == 1) {
@@ -983,8 +986,8 @@ cudaError_t gemm_tc(const GemmArgs& g, int mode, void* ws, size_t ws_bytes, cuda
         e = cudaMemsetAsync(rmA, 0, (size_t)Mp * nb * 8, s);
         if (e == cudaSuccess && nsides == 2) e = cudaMemsetAsync(rmB, 0, (size_t)Np * nb * 8, s);
         if (e != cudaSuccess) return e;
-        split_rowmax_kernel<<<dim3((Kp + 255) / 256, bands, nsides * nb), 256, 0, s>>>(opA, opB, rmA, rmB,
-                                                                                      nsides);
+        split_rowmax_kernel<<<dim3((Kp + kRowmaxSlab - 1) / kRowmaxSlab, bands, nsides * nb), 256, 0, s>>>(
+            opA, opB, rmA, rmB, nsides);
       }
       split_digits_kernel<<<dim3(Kp / 32, bands, nsides * nb), 256, 0, s>>>(
           opA, opB, rmA, rmB, (mode == TC_OZ && chunks > 1) ? Tacc : nullptr, Np, nsides);

@@ -32,6 +32,7 @@ GEMM_SHAPES = [
     (256, 384, 2048, False, False),   # two k chunks
     (129, 65, 97, True, True),        # ragged everything
     (1024, 8, 1024, False, False),    # narrow
+    (2048, 2048, 2048, False, False),  # the b = 2048 block product: 512 tiles, all SMs, no k split
 ]
 
 
