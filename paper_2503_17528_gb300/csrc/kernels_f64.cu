@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "bta_internal.cuh"
+#include "f64_device.cuh"
 #include "timing.cuh"
 
 namespace bta {
@@ -21,10 +22,6 @@ namespace bta {
 // Per-device info word: 1-based global row of the first non-positive pivot.
 // ---------------------------------------------------------------------------
 __device__ unsigned long long g_info;
-
-__device__ __forceinline__ void record_failure(long long row) {
-  atomicCAS(&g_info, 0ull, (unsigned long long)row);
-}
 
 cudaError_t info_reset(cudaStream_t s) {
   static const unsigned long long zero = 0;
@@ -49,21 +46,6 @@ cudaError_t info_read_reset(cudaStream_t s, long long* out) {
 // of 2x2 m8n8k4 fragments. Operands are staged through shared memory in 32-deep
 // k-chunks; ragged edges are zero-filled.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
-  asm volatile(
-      "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, "
-      "{%0,%1};\n"
-      : "+d"(c[0]), "+d"(c[1])
-      : "d"(a), "d"(b));
-}
-
-__device__ __forceinline__ double scale_by(double v, double alpha) {
-  if (alpha == 1.0) return v;
-  if (alpha == -1.0)
-    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
-  return alpha * v;
-}
-
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory");
   asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
@@ -423,88 +405,49 @@ cudaError_t gemm_f64(const GemmArgs& g, cudaStream_t s) {
 // POTRF of one diagonal tile; TRSM of the tiles below it; zeroing; mirroring.
 // ---------------------------------------------------------------------------
 
-// 1/sqrt(d) for d > 0 by Newton-Raphson on f(y) = 1/y^2 - d (y <- y (3 - d y^2) / 2),
-// seeded with the single-precision hardware estimate rsqrtf. Two steps take the
-// ~2^-23 seed error below FP64 rounding. Every dependent FP64 instruction is
-// expensive on this part, and this chain is about half the length of a
-// correctly rounded sqrt followed by a division; the pivot is then d * y.
-// A pivot outside the float range (binary exponent beyond +-100, or subnormal)
-// is first written d = d' 4^k with d' near 1 (exact power-of-two scaling), the
-// iteration runs on d', and y = y' 2^-k: an SPD matrix scaled by any power of
-// two factors like the unscaled one. Inf or NaN pivots are not rescaled and
-// come out NaN (0 * inf) in the pivot.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  const int e = (int)((__double_as_longlong(d) >> 52) & 0x7ff) - 1023;  // -1023: zero/subnormal
-  const int k = (e > 100 || e < -100) && e != 1024 ? e / 2 : 0;          // |k| <= 511
-  // 2^-2k and 2^-k as bit patterns: biased exponents 1023-2k in [1, 2045], 1023-k in [512, 1534].
-  const double ds = k ? d * __longlong_as_double((long long)(1023 - 2 * k) << 52) : d;
-  double y = (double)rsqrtf((float)ds);
-  const double h = 0.5 * ds;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
-  return k ? y * __longlong_as_double((long long)(1023 - k) << 52) : y;
+// One right-looking step k of a blocked Cholesky in two launches: the diagonal
+// tile (k, k) is factored and written back (recording a failed pivot), then the
+// tiles below it are solved against the written factor, X L_kk^T = A(r, k).
+// (A single launch in which the row tiles re-factor the diagonal tile while one
+// CTA writes it back is a race: CTAs of a launch need not run at the same time,
+// and a late one would read the factored tile.)
+__global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, int64_t ld, int64_t sb,
+                                                         int nrow, int k, long long row0,
+                                                         long long rstride) {
+  __shared__ double S[T][T + 1];
+  __shared__ double rd[T];
+  double* Ab = A + (int64_t)blockIdx.y * sb;
+  const int o = k * T, tb = min(T, nrow - o), tid = threadIdx.x;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    S[i][j] = (i < tb && j <= i) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
+  }
+  __syncthreads();
+  coop_factor(S, rd, tb, row0 + (long long)blockIdx.y * rstride + o, &g_info);
+  for (int e = tid; e < tb * tb; e += blockDim.x) {
+    const int i = e / tb, j = e % tb;
+    Ab[(int64_t)(o + i) * ld + o + j] = S[i][j];
+  }
 }
 
-// One right-looking step k of a blocked Cholesky, fused: CTA 0 factors the
-// diagonal tile (k,k) and writes it back (recording a failed pivot); CTA q >= 1
-// factors the same tile in shared memory (redundantly, nothing written) and
-// then solves its row tile r = k + q: X L_kk^T = A(r,k).
-__global__ void __launch_bounds__(256) potrf_panel_kernel(double* A, int64_t ld, int64_t sb,
-                                                          int nrow, int k, long long row0,
-                                                          long long rstride) {
-  __shared__ double S[T][T + 1];
+// Row tiles r = k + 1 + blockIdx.x of step k: X = A(r, k) L_kk^{-T}.
+__global__ void __launch_bounds__(256) trsm_panel_kernel(double* A, int64_t ld, int64_t sb,
+                                                         int nrow, int k) {
+  __shared__ double Lt[T][T + 1];
   __shared__ double X[T][T + 1];
   __shared__ double rd[T];
   double* Ab = A + (int64_t)blockIdx.y * sb;
   const int o = k * T, tb = min(T, nrow - o), tid = threadIdx.x;
-  const bool diag_cta = blockIdx.x == 0;
-  const int r0 = o + T * blockIdx.x, rows = diag_cta ? 0 : min(T, nrow - r0);
+  const int r0 = o + T * (blockIdx.x + 1), rows = min(T, nrow - r0);
   for (int e = tid; e < T * T; e += blockDim.x) {
     const int i = e / T, j = e % T;
-    S[i][j] = (i < tb && j <= i) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
-    if (!diag_cta) X[i][j] = (i < rows && j < tb) ? Ab[(int64_t)(r0 + i) * ld + o + j] : 0.0;
+    Lt[i][j] = (i < tb && j <= i) ? Ab[(int64_t)(o + i) * ld + o + j] : 0.0;
+    X[i][j] = (i < rows && j < tb) ? Ab[(int64_t)(r0 + i) * ld + o + j] : 0.0;
   }
   __syncthreads();
-  for (int j = 0; j < tb; ++j) {
-    if (tid == 0) {
-      double d = S[j][j];
-      if (!(d > 0.0)) {
-        if (diag_cta) record_failure(row0 + (long long)blockIdx.y * rstride + o + j + 1);
-        d = __longlong_as_double(0x7ff8000000000000ll);  // NaN poisons what follows
-      }
-      const double y = rsqrt_newton(d);
-      S[j][j] = d * y;
-      rd[j] = y;
-    }
-    __syncthreads();
-    const double r = rd[j];
-    for (int i = j + 1 + tid; i < tb; i += blockDim.x) S[i][j] *= r;
-    __syncthreads();
-    const int w = tb - j - 1;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c <= i) S[i][c] -= S[i][j] * S[c][j];
-    }
-    __syncthreads();
-  }
-  if (diag_cta) {
-    for (int e = tid; e < tb * tb; e += blockDim.x) {
-      const int i = e / tb, j = e % tb;
-      Ab[(int64_t)(o + i) * ld + o + j] = (j <= i) ? S[i][j] : 0.0;
-    }
-    return;
-  }
-  // Row tile: X = A(r,k) L_kk^{-T}, column sweep (rd[j] = 1 / L_jj).
-  for (int j = 0; j < tb; ++j) {
-    for (int i = tid; i < rows; i += blockDim.x) X[i][j] *= rd[j];
-    __syncthreads();
-    const int w = tb - j - 1;
-    for (int e = tid; e < rows * w; e += blockDim.x) {
-      const int i = e / w, c = j + 1 + e % w;
-      X[i][c] -= X[i][j] * S[c][j];
-    }
-    __syncthreads();
-  }
+  if (tid < tb) rd[tid] = 1.0 / Lt[tid][tid];
+  __syncthreads();
+  panel_solve(X, Lt, rd, rows, tb);
   for (int e = tid; e < rows * tb; e += blockDim.x) {
     const int i = e / tb, j = e % tb;
     Ab[(int64_t)(r0 + i) * ld + o + j] = X[i][j];
@@ -593,74 +536,6 @@ static inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a
 // caller reads the flag with bta_tc_status).
 // ---------------------------------------------------------------------------
 __device__ int g_wait_error;
-
-// Row of the lower-triangular index u (u = row (row + 1) / 2 + col, col <= row).
-__device__ __forceinline__ int tri_row(int u) {
-  int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-  while ((r + 1) * (r + 2) / 2 <= u) ++r;
-  while (r * (r + 1) / 2 > u) --r;
-  return r;
-}
-
-// Pivot of a tile Cholesky: L_jj = d y with y = 1 / sqrt(d); a non-positive
-// pivot is recorded (LAPACK-style row) and poisons the rest with NaN.
-__device__ __forceinline__ void pivot_of(double d, long long row, double& Ljj, double& y) {
-  if (!(d > 0.0)) {
-    record_failure(row);
-    d = __longlong_as_double(0x7ff8000000000000ll);
-  }
-  y = rsqrt_newton(d);
-  Ljj = d * y;
-}
-
-// Shared-memory Cholesky of a tb x tb tile in S (lower part valid); returns with
-// S = L (zero above) and rd[j] = 1 / L_jj. Records a failed pivot. Phase j
-// applies pivot j to the trailing triangle from the unscaled column j
-// (S_ic -= S_ij S_cj rd_j^2) and scales column j-1, while thread 0 finishes
-// diagonal entry j+1 and computes the next pivot: the pivot chain runs one step
-// ahead of the updates, one barrier per pivot. Needs more than one warp (the
-// updates run on warps 1 and up).
-__device__ void coop_factor(double (*S)[T + 1], double* rd, int tb, long long row_base) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  if (tid == 0) {
-    double L0, y0;
-    pivot_of(S[0][0], row_base + 1, L0, y0);
-    S[0][0] = L0;
-    rd[0] = y0;
-  }
-  __syncthreads();
-  for (int j = 0; j < tb; ++j) {
-    const double r = rd[j];
-    if (tid == 0) {
-      if (j + 1 < tb) {
-        const double sj = S[j + 1][j] * r;
-        double L1, y1;
-        pivot_of(fma(-sj, sj, S[j + 1][j + 1]), row_base + j + 2, L1, y1);
-        S[j + 1][j + 1] = L1;
-        rd[j + 1] = y1;
-      }
-    } else if (tid >= 32) {
-      const double r2 = r * r;
-      const int w = tb - j - 1, nel = w * (w + 1) / 2;
-      for (int e = tid - 32; e < nel; e += nthr - 32) {
-        const int rr = tri_row(e), cc = e - rr * (rr + 1) / 2;
-        if (rr == 0) continue;  // (j+1, j+1): thread 0's
-        const int i = j + 1 + rr, c = j + 1 + cc;
-        S[i][c] = fma(-S[i][j] * S[c][j], r2, S[i][c]);
-      }
-    }
-    if (j > 0) {  // column j-1 is no longer read: scale it
-      const double rp = rd[j - 1];
-      for (int i = j + tid; i < tb; i += nthr) S[i][j - 1] *= rp;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < T * T; e += nthr) {
-    const int i = e / T, c = e % T;
-    if (c > i) S[i][c] = 0.0;
-  }
-  __syncthreads();
-}
 
 // ---------------------------------------------------------------------------
 // One block step i of the factorization (Algorithm 1) in one cooperative
@@ -755,22 +630,6 @@ __device__ __forceinline__ double* ext_tile(const StepArgs& p, int r, int c, int
   ld = p.ld;
   double* base = gc == 0 ? (gr == 0 ? p.D0 : p.Lw) : p.D1;
   return base + (int64_t)(T * lr) * p.ld + T * lc;
-}
-
-// Panel solve in shared memory: X (rows x tb) <- X L^{-T}, L lower in Lt, rdv = 1 / diag(L).
-__device__ __forceinline__ void panel_solve(double (*X)[T + 1], const double (*Lt)[T + 1],
-                                            const double* rdv, int rows, int tb) {
-  const int tid = threadIdx.x;
-  for (int j = 0; j < tb; ++j) {
-    if (tid < rows) X[tid][j] *= rdv[j];
-    __syncthreads();
-    const int w = tb - j - 1;
-    for (int e = tid; e < rows * w; e += blockDim.x) {
-      const int i = e / w, c = j + 1 + e % w;
-      X[i][c] -= X[i][j] * Lt[c][j];
-    }
-    __syncthreads();
-  }
 }
 
 // Bounded wait until *flag >= v (a flag another CTA of the same cooperative
@@ -926,7 +785,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p
         S[i][j] = (i < tb && j <= i) ? Dc[(int64_t)i * b + j] : 0.0;
       }
       __syncthreads();
-      coop_factor(S, rd, tb, p.row0 + (long long)c * T);
+      coop_factor(S, rd, tb, p.row0 + (long long)c * T, &g_info);
       for (int e = tid; e < T * T; e += blockDim.x) {
         const int i = e / T, j = e % T;
         if (i < tb && j < tb) Dc[(int64_t)i * b + j] = S[i][j];
@@ -1105,8 +964,11 @@ cudaError_t potrf_blocks(double* A, int64_t ld, int64_t sb, int count, int nrow,
     for (int k = 0; k < nt; ++k) {
       {
         TimedLaunch tl(K_POTRF_TILE, 0.0, s);
-        potrf_panel_kernel<<<dim3(nt - k, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k, r0,
-                                                             info_rstride);
+        potrf_tile_kernel<<<dim3(1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k, r0, info_rstride);
+      }
+      if (k + 1 < nt) {
+        TimedLaunch tl(K_TRSM_PANEL, 0.0, s);
+        trsm_panel_kernel<<<dim3(nt - k - 1, cnt), 256, 0, s>>>(Ac, ld, sb, nrow, k);
       }
       if (k + 1 < nt) {
         const int o = (k + 1) * T, m = nrow - o;

@@ -68,3 +68,22 @@ def test_autotuner_measures_and_caches(tmp_path, monkeypatch):
     assert res["nstreams"] in (1, 4) and res["policy"] in ("fp64", "ozaki_b256")
     assert len(res["table"]) == 4 and all(r["ms"] > 0 for r in res["table"])
     assert tune.lookup(mats)["nstreams"] == res["nstreams"]
+
+
+def test_many_streams_uneven_batch_matches_oracle():
+    """Shapes drawn like the benchmark batch (b in {128, 256, 512}) on 16
+    concurrent library streams. Under that load the CTAs of one launch start at
+    different times, which exposes any kernel that reads in one CTA what another
+    CTA of the same launch writes (the small-b POTRF step once did)."""
+    rng = np.random.default_rng(5)
+    shapes = [(int(rng.integers(20, 41)), int(rng.choice([128, 256, 512])), int(rng.choice([2, 4, 8])))
+              for _ in range(24)]
+    raw = [gen.make_bta(n, b, a, seed=700 + k, shift=gen.SHIFT_1_01) for k, (n, b, a) in enumerate(shapes)]
+    mats = [tuple(dev(x) for x in m) for m in raw]
+    lds = Batch(mats, policy="fp64", nstreams=16).run()
+    torch.cuda.synchronize()
+    assert bta.get_info() == 0 and bta.tc_status() == 0
+    for (d, l, ar, t), m, ld in zip(raw, mats, host(lds)):
+        F = oracle.pobtaf(d, l, ar, t)
+        assert abs(ld - oracle.logdet(F)) <= TOL * abs(oracle.logdet(F))
+        assert worst_block_error([host(x) for x in m], oracle.pobtasi(F)) <= TOL
