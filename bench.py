@@ -68,7 +68,7 @@ def flops_solve(n, b, a, r):
 
 
 KERNELS = ["gemm_f64", "potrf_panel", "trsm_panel", "tile_inv", "zero_upper", "mirror", "logdet", "trsv",
-           "gemv", "arrow", "probe", "gemm_tc", "tc_split", "tc_final", "factor_step"]
+           "gemv", "arrow", "probe", "gemm_tc", "tc_split", "tc_final", "factor_step", "persistent"]
 # tensor-core products per FP64 product in each precision mode
 TC_PAIRS = {"ozaki": 28, "bf16x3": 3}
 PREC_DTYPE = {"fp64": "f64", "ozaki": "bf16 slices x7 (FP64-emulated, Ozaki splitting)",
@@ -90,15 +90,37 @@ def measured_peaks():
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, summed over the kernel's launches of one step in one ncu
 # capture and divided by their number), keyed by kernel name. Each entry names
-# the source file the kernel lives in and a digest of that file at capture time:
-# once the source changes, the figure no longer describes the kernel and the
-# bench line reports traffic as null.
-TRAFFIC = {}
+# the source file of the kernel and a digest of the kernel's own source text
+# (its __global__ definition, brace-matched) at capture time: once that text
+# changes, the figure no longer describes the kernel and the bench line reports
+# traffic as null.
+TRAFFIC = {
+    "gemm_f64": {"workload": "n256_b2048_a16", "source": "kernels_f64.cu", "symbol": "gemm_f64_kernel",
+                 "digest": "780b5ba4e92474a9", "bytes_per_launch": 180.3e6,
+                 "capture": "profiles/launches_n256_b2048_a16_fp64.md: 526 launches of one step, "
+                            "132.5 MB read + 47.8 MB written per launch on average"},
+}
 
 
-def _source_digest(rel):
-    with open(os.path.join(ROOT, "paper_2503_17528_gb300", "csrc", rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_source(src, symbol):
+    """Text of the __global__ function `symbol` in `src` (brace-matched)."""
+    i = src.index(symbol + "(")
+    i = src.rfind("__global__", 0, i)
+    j = src.index("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        if src[k] == "{":
+            depth += 1
+        elif src[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return src[i:k + 1]
+    raise ValueError(symbol)
+
+
+def kernel_digest(rel, symbol):
+    with open(os.path.join(ROOT, "paper_2503_17528_gb300", "csrc", rel)) as f:
+        return hashlib.sha256(kernel_source(f.read(), symbol).encode()).hexdigest()[:16]
 
 
 def traffic_of(kernel, workload):
@@ -106,9 +128,9 @@ def traffic_of(kernel, workload):
     if not e or e.get("workload") != workload:
         return None
     try:
-        if _source_digest(e["source"]) != e["digest"]:
+        if kernel_digest(e["source"], e["symbol"]) != e["digest"]:
             return None
-    except OSError:
+    except (OSError, ValueError):
         return None
     return {"bytes_per_launch": e["bytes_per_launch"], "capture": e["capture"]}
 
@@ -315,7 +337,7 @@ def batch_measure(steps, warmup, dev, rank=0, world=1, oracle_sample=0, quick_tu
     import torch
     import paper_2503_17528_gb300 as bta
     from paper_2503_17528_gb300 import tune
-    from paper_2503_17528_gb300.batched import Batch
+    from paper_2503_17528_gb300.batched import Batch, PersistentBatch
     raw_all = make_batch()
     fl_all = [flops_factor(m[0].shape[0], m[0].shape[1], m[3].shape[0]) +
               flops_selinv(m[0].shape[0], m[0].shape[1], m[3].shape[0]) for m in raw_all]
@@ -393,24 +415,70 @@ def batch_measure(steps, warmup, dev, rank=0, world=1, oracle_sample=0, quick_tu
            else "bf16 slices (FP64-emulated)",
            "max_block_rel_err_vs_sequential_fp64": float(f"{worst:.3e}")}
     if oracle_sample:
-        # The first few matrices of the batched result against the oracle.
-        import oracle
-        ow = 0.0
-        ld_err = 0.0
-        logdets = batch.logdets.cpu().numpy()
-        for k in range(min(oracle_sample, len(raw))):
-            F = oracle.pobtaf(*raw[k])
-            X = oracle.pobtasi(F)
-            for x, y in zip(W[k], X):
-                if y.size:
-                    ow = max(ow, blockerr(x.cpu(), torch.from_numpy(y)))
-            ldo = oracle.logdet(F)
-            ld_err = max(ld_err, abs(float(logdets[k]) - ldo) / abs(ldo))
-        out["oracle_check"] = {"matrices": min(oracle_sample, len(raw)),
-                               "max_block_rel_err_vs_oracle": float(f"{ow:.3e}"),
-                               "max_logdet_rel_err_vs_oracle": float(f"{ld_err:.3e}")}
+        out["oracle_check"] = _batch_oracle_check(raw, W, batch.logdets, oracle_sample)
+    # The persistent form: the whole batch in one cooperative launch (FP64),
+    # parameters from the autotuner (cached, else a short search now).
+    pcfg = tune.lookup_persistent(W)
+    ptuned_now = pcfg is None
+    if pcfg is None:
+        pcfg = tune.tune_persistent(W, P, candidates=PERSISTENT_QUICK if quick_tune else None, reps=1,
+                                    save=not quick_tune)
+    pb = PersistentBatch(W, **pcfg["params"])
+    reset()
+    pb.run()
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(side):
+        pgraph = pb.capture()
+    torch.cuda.current_stream(dev).wait_stream(side)
+
+    def preplay():
+        reset()
+        pgraph.replay()
+
+    pers_ms = timed(preplay, steps)
+    timed_out, info = pb.status()
+    pworst = 0.0
+    for w, r in zip(W, seq_out):
+        for x, y in zip(w, r):
+            if y.numel():
+                pworst = max(pworst, blockerr(x, y))
+    pers = {"ms_per_batch": round(pers_ms, 3), "speedup_vs_sequential": round(seq_ms / pers_ms, 3),
+            "speedup_vs_multistream_graph": round(graph_ms / pers_ms, 3),
+            "tflops": round(flops / (pers_ms * 1e-3) / 1e12, 4), "dtype": "f64",
+            "launches_per_batch": 1, "plan": pb.describe(), "tuned": pcfg["params"],
+            "tuned_in_this_run": ptuned_now, "tuning_table": pcfg.get("table"),
+            "timed_out": timed_out, "failed_matrices": sum(1 for v in info if v),
+            "max_block_rel_err_vs_sequential_fp64": float(f"{pworst:.3e}"),
+            "logdet_max_rel_err_vs_sequential_fp64": float(f"{float(((pb.logdets - seq_ld).abs() / seq_ld.abs()).max()):.3e}")}
+    if oracle_sample:
+        pers["oracle_check"] = _batch_oracle_check(raw, W, pb.logdets, oracle_sample)
+    out["persistent"] = pers
+    del pgraph
+    pb.close()
     del seq_ld
     return out
+
+
+PERSISTENT_QUICK = ((8, 0, 1), (4, 0, 1), (4, 0, 2), (8, 16, 1))
+
+
+def _batch_oracle_check(raw, W, logdets, sample):
+    """The first few matrices of a batched result against the oracle."""
+    import torch
+    import oracle
+    ow = 0.0
+    ld_err = 0.0
+    lds = logdets.cpu().numpy()
+    for k in range(min(sample, len(raw))):
+        F = oracle.pobtaf(*raw[k])
+        X = oracle.pobtasi(F)
+        for x, y in zip(W[k], X):
+            if y.size:
+                ow = max(ow, blockerr(x.cpu(), torch.from_numpy(y)))
+        ldo = oracle.logdet(F)
+        ld_err = max(ld_err, abs(float(lds[k]) - ldo) / abs(ldo))
+    return {"matrices": min(sample, len(raw)), "max_block_rel_err_vs_oracle": float(f"{ow:.3e}"),
+            "max_logdet_rel_err_vs_oracle": float(f"{ld_err:.3e}")}
 
 
 def run_batch(args, rank=0, world=1, local_rank=0):

@@ -197,6 +197,78 @@ size_t bta_batch_workspace_bytes(int64_t n, int64_t b, int64_t a, int prec);
 int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int nstreams,
                               bta_stream_t stream);
 
+/* ---- Persistent batched form --------------------------------------------- */
+
+/*
+ * A plan runs factorization (Algorithm 1), log-det and selected inversion
+ * (Algorithm 2, Section 2.2) of `count` independent FP64 BTA matrices of any
+ * n, b, a in ONE persistent cooperative kernel launch (not in the paper; the
+ * batched form of the same method). Each matrix's work is a chain of
+ * operations made of 32 x 32 tile items (the block step's tile Cholesky with
+ * its Schur updates, the tip, the inverses L_ii^{-1}, the products G_i, H_i,
+ * M_i, X_nn and the backward recurrence); a host-side list scheduler merges the
+ * matrices' operations into one order and the kernel's CTAs take items from it,
+ * each waiting (bounded) on per-operation completion counters.
+ *
+ * Tuning parameters (0 = automatic):
+ *   ctas_per_sm    resident CTAs per SM (128 threads each; capped by occupancy)
+ *   lanes          matrices in flight: the scheduler spreads the matrices over
+ *                  this many lanes of grid/lanes CTAs each (0: the count with
+ *                  the shortest simulated makespan)
+ *   rows_per_item  1 or 2 tile rows per update / product item (tile shape
+ *                  32 x 32 or 64 x 32)
+ */
+typedef struct bta_plan_params {
+  int ctas_per_sm;
+  int lanes;
+  int rows_per_item;
+  int reserved;
+} bta_plan_params;
+
+typedef struct bta_plan_s* bta_plan;
+
+/* Workspace per matrix: L_ii^{-1} [n][b][b], G [n-1][b][b], H [n][a][b],
+ * L_nn^{-1} [a][a], pivot reciprocals and per-tile log sums, 256-byte aligned
+ * parts. 0 for invalid sizes. */
+size_t bta_plan_entry_workspace_bytes(int64_t n, int64_t b, int64_t a);
+
+/*
+ * bta_plan_create -- builds the schedule for `entries` (their pointers are
+ * baked into the plan: a plan runs on exactly those buffers) and allocates its
+ * device tables (cudaMalloc, on the current device, which must hold the
+ * buffers). Entries: prec must be BTA_PREC_FP64; ws of at least
+ * bta_plan_entry_workspace_bytes(n, b, a) bytes, 256-byte aligned; logdet_out
+ * may be NULL. params may be NULL (all automatic). Synchronous. Returns 0 and
+ * *out, -1 for count out of [1, 65536], -2 for an invalid entry, -3 for invalid
+ * params, -4 for a NULL out, > 0 for a CUDA error.
+ */
+int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_plan_params* params,
+                    bta_plan* out);
+
+/*
+ * bta_plan_run -- enqueues one run on `stream` (a counter reset and one
+ * cooperative launch; capturable in a CUDA graph): every matrix A -> X in
+ * place, log det A to its logdet_out. The stream must belong to the plan's
+ * device (-1 otherwise). Runs of one plan must not overlap.
+ */
+int bta_plan_run(bta_plan plan, bta_stream_t stream);
+
+/*
+ * bta_plan_status -- synchronizes `stream` and reports the last run: *timed_out
+ * = 1 if a dependency wait ran out (the results are then invalid), and, if info
+ * is not NULL, info[k] = 1-based row of matrix k's first non-positive pivot (0:
+ * none; LAPACK-style, as bta_get_info).
+ */
+int bta_plan_status(bta_plan plan, int* timed_out, int64_t* info, bta_stream_t stream);
+
+/* bta_plan_describe -- out[0..nout-1] = grid CTAs, CTAs per SM, lanes, rows per
+ * item, operations, items, algorithmic flops per run, simulated makespan. */
+int bta_plan_describe(bta_plan plan, int64_t* out, int nout);
+
+/* bta_plan_destroy -- frees the plan's device tables (synchronously; no run of
+ * the plan may be pending). NULL is a no-op. */
+int bta_plan_destroy(bta_plan plan);
+
 /* ---- Partitioned form (the paper's Sections 3.1-3.4 on one device) ------- */
 
 /*
@@ -366,6 +438,7 @@ int bta_wait_selftest(int64_t polls, int* timed_out);
 #define BTA_KERNEL_TC_SPLIT 12 /* FP64 -> BF16 slice splitting */
 #define BTA_KERNEL_TC_FINAL 13 /* int64 accumulator -> FP64 output */
 #define BTA_KERNEL_FACTOR_STEP 14 /* one fused block step of the FP64 factorization */
+#define BTA_KERNEL_PERSISTENT 15  /* one run of a persistent batched plan (bta_plan_run) */
 
 /*
  * bta_timing_enable -- on != 0: from now on every kernel launch of the library

@@ -52,12 +52,23 @@ _SIGS = {
     "bta_factor_selinv_all": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _p, _sz, _p],
     "bta_factor_selinv_host": [_i64, _i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p, _p, _p,
                                _p, _sz, _p],
+    "bta_plan_entry_workspace_bytes": [_i64, _i64, _i64],
+    "bta_plan_create": [_i64, _p, _p, _p],
+    "bta_plan_run": [_p, _p],
+    "bta_plan_status": [_p, ctypes.POINTER(ctypes.c_int), _p, _p],
+    "bta_plan_describe": [_p, ctypes.POINTER(_i64), ctypes.c_int],
+    "bta_plan_destroy": [_p],
     "bta_version": [],
 }
 
 class BatchEntry(ctypes.Structure):
     _fields_ = [("n", _i64), ("b", _i64), ("a", _i64), ("diag", _p), ("lower", _p), ("arrow", _p),
                 ("tip", _p), ("logdet_out", _p), ("prec", ctypes.c_int), ("ws", _p), ("ws_bytes", _sz)]
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("lanes", ctypes.c_int), ("rows_per_item", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _lib = None

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbta.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels_f64.cu", "kernels_tc.cu", "bta_api.cu", "timing.cu", "noalloc.cu"]
+SOURCES = ["kernels_f64.cu", "kernels_tc.cu", "bta_api.cu", "timing.cu", "noalloc.cu",
+           "batch_persistent.cu"]
 
 
 def nvcc_path() -> str:

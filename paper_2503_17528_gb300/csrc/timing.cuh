@@ -24,6 +24,7 @@ enum KernelId {
   K_TC_SPLIT,
   K_TC_FINAL,
   K_FACTOR_STEP,
+  K_PERSISTENT,
   K_COUNT
 };
 

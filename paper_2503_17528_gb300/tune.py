@@ -83,3 +83,63 @@ def tune(mats, pristine, policies=None, streams=STREAMS, reps=2, save=True):
             json.dump(cache, f, indent=1)
     restore()
     return res
+
+
+# Candidates of the persistent kernel: (CTAs per SM, lanes = matrices in flight,
+# tile rows per item). Two tile rows need the 4-CTAs-per-SM register budget.
+PERSISTENT_CANDIDATES = tuple((c, w, r) for r in (1, 2) for c in ((4, 8) if r == 1 else (2, 4))
+                              for w in (0, 8, 16, 32))
+
+
+def tune_persistent(mats, pristine, candidates=None, reps=2, save=True):
+    """Times each (ctas_per_sm, lanes, rows_per_item) candidate of the persistent
+    batched kernel on the actual batch (graph replays) and caches the fastest
+    under the key 'persistent|' + signature. Returns {"params", "ms", "table"}."""
+    from .batched import PersistentBatch
+    table = []
+
+    def restore():
+        for w, p in zip(mats, pristine):
+            for x, y in zip(w, p):
+                if x is not None and x.numel():
+                    x.copy_(y)
+
+    for cps, lanes, rows in (candidates or PERSISTENT_CANDIDATES):
+        pb = PersistentBatch(mats, ctas_per_sm=cps, lanes=lanes, rows_per_item=rows)
+        restore()
+        pb.run()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            graph = pb.capture()
+        torch.cuda.current_stream().wait_stream(side)
+        times = []
+        for _ in range(reps):
+            restore()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        desc = pb.describe()
+        del graph
+        pb.close()
+        table.append({"ctas_per_sm": desc["ctas_per_sm"], "lanes": desc["lanes"], "rows_per_item": rows,
+                      "requested_lanes": lanes, "ms": min(times)})
+    best = min(table, key=lambda r: r["ms"])
+    res = {"params": {"ctas_per_sm": best["ctas_per_sm"], "lanes": best["lanes"],
+                      "rows_per_item": best["rows_per_item"]}, "ms": best["ms"], "table": table}
+    if save:
+        cache = _load()
+        cache["persistent|" + signature(mats)] = res
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    restore()
+    return res
+
+
+def lookup_persistent(mats):
+    return _load().get("persistent|" + signature(mats))

@@ -45,3 +45,15 @@ def test_solve_byte_model_hand_count(bench):
     # written in each of the two sweeps.
     assert bench.solve_bytes(2, 2, 1, 1) == 8 * (2 * 15 + 4 * 5)
     assert bench.solve_bytes(365, 1024, 8, 4) == pytest.approx(9.27e9, rel=1e-3)
+
+
+def test_traffic_table_names_live_kernels(bench):
+    """Every stored DRAM-traffic figure names a kernel whose source text is found,
+    and is reported only while that text is unchanged since the capture."""
+    for name, e in bench.TRAFFIC.items():
+        assert e["bytes_per_launch"] > 0 and e["capture"].startswith("profiles/")
+        assert os.path.exists(os.path.join(ROOT, e["capture"].split(":")[0]))
+        assert len(bench.kernel_digest(e["source"], e["symbol"])) == 16
+        live = bench.kernel_digest(e["source"], e["symbol"]) == e["digest"]
+        assert (bench.traffic_of(name, e["workload"]) is not None) == live
+        assert bench.traffic_of(name, "another_workload") is None

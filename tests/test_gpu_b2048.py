@@ -100,3 +100,22 @@ def test_n256_b2048_a16_full_parity():
             worst = max(worst, rel_fro(host(Lo[i]), Xl[i]))
     worst = max(worst, rel_fro(host(Ti), Xt))
     assert worst <= TOL, worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_dataset4_block_shape_parity(prec):
+    """Block order b = 2865, a = 4 (the shape of the paper's weak-scaling dataset,
+    Section 5.2): 90 tiles per block row with a 17-row ragged last tile, so every
+    tile kernel runs its ragged edges at scale (Ozaki: halves of 1432 and 1433)."""
+    bta.set_precision(prec)
+    n, b, a = 3, 2865, 4
+    d, l, ar, t = gen.make_bta(n, b, a, seed=2865, shift=gen.SHIFT_1_01)
+    r = gen.make_rhs(n, b, a, nrhs=4, seed=2866)
+    Lg, ldg, xg, Xg = _run_four_calls(d, l, ar, t, r)
+    assert bta.tc_status() == 0 and bta.get_info() == 0
+    F = oracle.pobtaf(d, l, ar, t)
+    assert worst_block_error(Lg, (F.diag, F.lower, F.arrow, F.tip)) <= TOL
+    ldo = oracle.logdet(F)
+    assert abs(ldg - ldo) <= TOL * abs(ldo)
+    assert rel_fro(xg, oracle.solve(F, r)) <= TOL
+    assert worst_block_error(Xg, oracle.pobtasi(F)) <= TOL
