@@ -203,24 +203,24 @@ int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int
  * A plan runs factorization (Algorithm 1), log-det and selected inversion
  * (Algorithm 2, Section 2.2) of `count` independent FP64 BTA matrices of any
  * n, b, a in ONE persistent cooperative kernel launch (not in the paper; the
- * batched form of the same method). Each matrix's work is a chain of
+ * batched form of the same method). Each matrix's work is a graph of
  * operations made of 32 x 32 tile items (the block step's tile Cholesky with
  * its Schur updates, the tip, the inverses L_ii^{-1}, the products G_i, H_i,
- * M_i, X_nn and the backward recurrence); a host-side list scheduler merges the
- * matrices' operations into one order and the kernel's CTAs take items from it,
- * each waiting (bounded) on per-operation completion counters.
+ * M_i, X_nn and the backward recurrence). On the device an operation becomes
+ * ready when the operations it depends on have completed; the kernel's CTAs
+ * take items of ready operations from two queues (small operations first), so
+ * no CTA waits for a particular item.
  *
  * Tuning parameters (0 = automatic):
  *   ctas_per_sm    resident CTAs per SM (128 threads each; capped by occupancy)
- *   lanes          matrices in flight: the scheduler spreads the matrices over
- *                  this many lanes of grid/lanes CTAs each (0: the count with
- *                  the shortest simulated makespan)
+ *   small_items    operations with at most this many items go to the priority
+ *                  queue (0: 32)
  *   rows_per_item  1 or 2 tile rows per update / product item (tile shape
  *                  32 x 32 or 64 x 32)
  */
 typedef struct bta_plan_params {
   int ctas_per_sm;
-  int lanes;
+  int small_items;
   int rows_per_item;
   int reserved;
 } bta_plan_params;
@@ -233,7 +233,7 @@ typedef struct bta_plan_s* bta_plan;
 size_t bta_plan_entry_workspace_bytes(int64_t n, int64_t b, int64_t a);
 
 /*
- * bta_plan_create -- builds the schedule for `entries` (their pointers are
+ * bta_plan_create -- builds the operation graph of `entries` (their pointers are
  * baked into the plan: a plan runs on exactly those buffers) and allocates its
  * device tables (cudaMalloc, on the current device, which must hold the
  * buffers). Entries: prec must be BTA_PREC_FP64; ws of at least
@@ -255,14 +255,16 @@ int bta_plan_run(bta_plan plan, bta_stream_t stream);
 
 /*
  * bta_plan_status -- synchronizes `stream` and reports the last run: *timed_out
- * = 1 if a dependency wait ran out (the results are then invalid), and, if info
+ * = 1 if the kernel gave up waiting for work (no operation completed for
+ * seconds; the results are then invalid), and, if info
  * is not NULL, info[k] = 1-based row of matrix k's first non-positive pivot (0:
  * none; LAPACK-style, as bta_get_info).
  */
 int bta_plan_status(bta_plan plan, int* timed_out, int64_t* info, bta_stream_t stream);
 
-/* bta_plan_describe -- out[0..nout-1] = grid CTAs, CTAs per SM, lanes, rows per
- * item, operations, items, algorithmic flops per run, simulated makespan. */
+/* bta_plan_describe -- out[0..nout-1] = grid CTAs, CTAs per SM, priority
+ * threshold (items), rows per item, operations, items, algorithmic flops per
+ * run, operations ready at the start. */
 int bta_plan_describe(bta_plan plan, int64_t* out, int nout);
 
 /* bta_plan_destroy -- frees the plan's device tables (synchronously; no run of

@@ -22,25 +22,24 @@
 //     X_ii      =  M_i - X_{i+1,i}^T G_i - X_{n,i}^T H_i   (lower tiles, mirrored)
 // An operation depends on at most four earlier operations of the same matrix.
 //
-// The operations of all matrices are merged into one global order by a
-// host-side list scheduler: the matrices are spread over W lanes (largest
-// first, each to the least-loaded lane), each lane is simulated as a machine of
-// G / W CTAs running its operations one after another, and the operations are
-// ordered by their simulated start times. W (the matrices in flight, so G / W
-// CTAs per matrix), the CTAs per SM and R (tile rows per item) are the tuning
-// parameters.
-//
-// On the device every CTA repeatedly takes the next item in that order (a
-// cursor over the operations and a per-operation counter of taken items),
-// waits until the operation's dependencies have completed all their items
-// (per-operation done counters), runs the item and counts it done. Items are
-// taken in order and an operation depends only on earlier ones, so the item
-// with the lowest unfinished position can always run: with every CTA resident
-// (cooperative launch) the schedule cannot deadlock. Every wait is bounded: a
-// wait that runs out sets the plan's error word and the CTA goes on, and later
-// waits give up at once, so the launch always ends. Data written by one item
-// and read by another is read through L2 (ld.global.cg): items of the same
-// tile can run on different SMs, whose L1 caches are not coherent.
+// Scheduling is dynamic, on the device. An operation is ready once all the
+// operations it depends on have completed; ready operations wait in two FIFO
+// queues, a priority queue for small operations (at most `small_items` items:
+// the tile factorizations, panel solves and most of the recurrence, which gate
+// a matrix's progress) and a bulk queue. Every CTA repeatedly takes the next
+// item of the first ready operation that still has items (priority queue
+// first), runs it and counts it done; the CTA that completes an operation
+// counts one more finished dependency in each of its successors and appends
+// those that become ready to their queue. No CTA waits for a particular item:
+// a CTA that finds both queues empty polls until an operation completes, so
+// the kernel cannot deadlock, and it ends when every operation has completed.
+// The poll is bounded: after many polls with no operation completing anywhere
+// it sets the plan's error word and the CTAs return. At the start the first
+// operation of every matrix is ready, the largest matrices first. Data written
+// by one item and read by another is read through L2 (ld.global.cg): items of
+// the same tile can run on different SMs, whose L1 caches are not coherent.
+// The tuning parameters are the CTAs per SM, R (tile rows per item) and the
+// priority threshold.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -101,7 +100,9 @@ struct PTrtri {
 
 struct POp {
   int kind, nitems, arg, k;
-  int dep[4];
+  int ndeps;              // operations that must complete before this one is ready
+  int succ_off, nsucc;    // the operations that depend on this one: succ[succ_off ..]
+  int prio;               // 0: priority queue (small operations), 1: bulk queue
 };
 
 struct PMat {
@@ -110,23 +111,31 @@ struct PMat {
   int nparts;
 };
 
+// Counters of a run (zeroed, then seeded with the initially ready operations).
+// hdr: [0] error word, [1] completed operations, then per queue q (0: priority,
+// 1: bulk) [2 + 2q] head and [3 + 2q] reserved slots. A queue entry is op + 1
+// (0: reserved, not written yet); every operation enters a queue once, so each
+// queue has nops slots.
 struct PDev {
   const POp* ops;
+  const int* succ;
   const PStep* steps;
   const PGemm* gemms;
   const PTrtri* trtris;
   const PMat* mats;
   int nops;
-  int* cursor;
-  int* error;
-  int* taken;
-  int* done;
-  unsigned long long* info;
+  int* hdr;
+  int* taken;      // [nops] items taken
+  int* done;       // [nops] items completed
+  int* sat;        // [nops] dependencies completed
+  int* queue;      // [2][nops]: queue q at queue + q * nops
+  unsigned long long* info;  // [matrices] first failed pivot row
   unsigned max_polls;
 };
 
 constexpr int kPThreads = 128;
 constexpr int kPMaxR = 2;
+constexpr int kCounterHeader = 64;  // ints of the run header (6 used)
 
 template <int MAXR>
 struct PSmem {
@@ -499,6 +508,66 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: the next ready item, the priority queue first; -1 when every
+// operation has completed (or a wait ran out). An idle CTA polls; it gives up
+// (error word) only after max_polls polls in which no operation completed.
+__device__ __forceinline__ int take_item(const PDev& d, int& item) {
+  unsigned idle = 0;
+  int seen = -1;
+  for (;;) {
+    for (int q = 0; q < 2; ++q) {
+      int* qh = d.hdr + 2 + 2 * q;
+      for (;;) {
+        const int h = ld_acquire(qh);
+        if (h >= ld_acquire(qh + 1)) break;  // empty
+        const int v = ld_acquire(d.queue + q * d.nops + h);
+        if (v == 0) break;  // reserved, being written: poll again
+        const int o = v - 1;
+        const int t = atomicAdd(d.taken + o, 1);
+        if (t < __ldg(&d.ops[o].nitems)) {
+          item = t;
+          return o;
+        }
+        atomicCAS(qh, h, h + 1);  // exhausted: move the head on
+      }
+    }
+    const int completed = ld_acquire(d.hdr + 1);
+    if (completed >= d.nops || ld_acquire(d.hdr) != 0) return -1;
+    if (completed != seen) {
+      seen = completed;
+      idle = 0;
+    } else if (++idle > d.max_polls) {
+      atomicExch(d.hdr, 1);
+      return -1;
+    }
+    __nanosleep(128);
+  }
+}
+
+// Thread 0, after this CTA's item of operation o is written: count it; the CTA
+// that completes the operation releases its successors into the queues.
+__device__ __forceinline__ void finish_item(const PDev& d, int o) {
+  __threadfence();
+  const POp& op = d.ops[o];
+  if (atomicAdd(d.done + o, 1) != __ldg(&op.nitems) - 1) return;
+  __threadfence();
+  const int so = __ldg(&op.succ_off), ns = __ldg(&op.nsucc);
+  for (int q = 0; q < ns; ++q) {
+    const int sidx = __ldg(d.succ + so + q);
+    const POp& sop = d.ops[sidx];
+    if (atomicAdd(d.sat + sidx, 1) == __ldg(&sop.ndeps) - 1) {
+      const int pq = __ldg(&sop.prio);
+      const int slot = atomicAdd(d.hdr + 3 + 2 * pq, 1);
+      st_release(d.queue + pq * d.nops + slot, sidx + 1);
+    }
+  }
+  atomicAdd(d.hdr + 1, 1);
+}
+
 // MINB: CTAs per SM the register budget is sized for; MAXR: largest R.
 template <int MINB, int MAXR>
 __global__ void __launch_bounds__(kPThreads, MINB) persistent_kernel(PDev d) {
@@ -506,35 +575,8 @@ __global__ void __launch_bounds__(kPThreads, MINB) persistent_kernel(PDev d) {
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
-      int o = -1, it = 0;
-      for (;;) {
-        const int c = ld_acquire(d.cursor);
-        if (c >= d.nops) break;
-        const int t = atomicAdd(d.taken + c, 1);
-        if (t < __ldg(&d.ops[c].nitems)) {
-          o = c;
-          it = t;
-          break;
-        }
-        atomicCAS(d.cursor, c, c + 1);
-      }
-      if (o >= 0) {
-        for (int q = 0; q < 4; ++q) {
-          const int dp = __ldg(&d.ops[o].dep[q]);
-          if (dp < 0) continue;
-          const int need = __ldg(&d.ops[dp].nitems);
-          unsigned polls = 0;
-          while (ld_acquire(d.done + dp) < need) {
-            if (++polls > d.max_polls || *(volatile int*)d.error) {
-              atomicExch(d.error, 1);
-              break;
-            }
-            __nanosleep(256);
-          }
-        }
-        __threadfence();
-      }
-      sm.op = o;
+      int it = 0;
+      sm.op = take_item(d, it);
       sm.item = it;
     }
     __syncthreads();
@@ -552,10 +594,7 @@ __global__ void __launch_bounds__(kPThreads, MINB) persistent_kernel(PDev d) {
       default: break;
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(d.done + o, 1);
-    }
+    if (tid == 0) finish_item(d, o);
   }
 }
 
@@ -583,7 +622,7 @@ size_t entry_ws(int64_t n, int64_t b, int64_t a, void* base, EntryWs* o) {
 
 struct HOp {
   POp op;
-  double tau;  // estimated item time (DMMA 32^3 chunk units)
+  int dep[4];  // local indices of the operations this one depends on (-1: none)
   int local;   // position in the matrix's program
 };
 
@@ -595,24 +634,17 @@ struct Builder {
   int R = 1;
 
   // Appends an op; deps are local indices into `ops` (-1: none).
-  static int add(std::vector<HOp>& ops, int kind, int nitems, int arg, int k, double tau,
-                 int d0 = -1, int d1 = -1, int d2 = -1, int d3 = -1) {
+  static int add(std::vector<HOp>& ops, int kind, int nitems, int arg, int k, int d0 = -1,
+                 int d1 = -1, int d2 = -1, int d3 = -1) {
     HOp h{};
     h.op.kind = kind;
     h.op.nitems = nitems;
     h.op.arg = arg;
     h.op.k = k;
-    h.op.dep[0] = d0; h.op.dep[1] = d1; h.op.dep[2] = d2; h.op.dep[3] = d3;
-    h.tau = tau;
+    h.dep[0] = d0; h.dep[1] = d1; h.dep[2] = d2; h.dep[3] = d3;
     h.local = (int)ops.size();
     ops.push_back(h);
     return h.local;
-  }
-
-  static double gemm_tau(const PGemm& g) {
-    double ch = 0.0;
-    for (int q = 0; q < g.nterms; ++q) ch += (g.t[q].K + T - 1) / T;
-    return 0.2 + ch * (g.lowerC ? 1 : g.R);
   }
 
   int gemm_items(PGemm& g) {
@@ -628,7 +660,7 @@ struct Builder {
   int add_gemm(std::vector<HOp>& ops, PGemm g, int d0, int d1 = -1, int d2 = -1, int d3 = -1) {
     const int items = gemm_items(g);
     gemms.push_back(g);
-    return add(ops, PK_GEMM, items, (int)gemms.size() - 1, 0, gemm_tau(g), d0, d1, d2, d3);
+    return add(ops, PK_GEMM, items, (int)gemms.size() - 1, 0, d0, d1, d2, d3);
   }
 
   // Tile Cholesky ops of one step, chained after `prev`; returns the last op.
@@ -636,11 +668,11 @@ struct Builder {
     steps.push_back(p);
     const int s = (int)steps.size() - 1;
     for (int k = 0; k < p.nt; ++k) {
-      prev = add(ops, PK_POTRF, 1, s, k, 0.6, prev);
-      if (p.E - k - 1 > 0) prev = add(ops, PK_PANEL, p.E - k - 1, s, k, 0.6, prev);
+      prev = add(ops, PK_POTRF, 1, s, k, prev);
+      if (p.E - k - 1 > 0) prev = add(ops, PK_PANEL, p.E - k - 1, s, k, prev);
       int items = 0;
       for (int c = k + 1; c < p.Ecol; ++c) items += (p.E - c + R - 1) / R;
-      if (items > 0) prev = add(ops, PK_UPDATE, items, s, (k << 4) | R, 0.15 + R, prev);
+      if (items > 0) prev = add(ops, PK_UPDATE, items, s, (k << 4) | R, prev);
     }
     return prev;
   }
@@ -696,12 +728,12 @@ struct Builder {
     }
     const int fac = prev;
     mats.push_back(PMat{w.ldpart, e.logdet_out, (int)(n * nt + na)});
-    add(ops, PK_LOGDET, 1, (int)mats.size() - 1, 0, 0.3, fac);
+    add(ops, PK_LOGDET, 1, (int)mats.size() - 1, 0, fac);
     // L_ii^{-1} of every block.
     trtris.push_back(PTrtri{e.diag, w.Linv, b, bb, B, nt, (int)n});
     const int tb = (int)trtris.size() - 1;
-    int tr = add(ops, PK_TINV, (int)n * nt, tb, 0, 0.6, fac);
-    for (int r = 1; r < nt; ++r) tr = add(ops, PK_TRTRI, (int)n * r, tb, r, 1.2 + 0.5 * r, tr);
+    int tr = add(ops, PK_TINV, (int)n * nt, tb, 0, fac);
+    for (int r = 1; r < nt; ++r) tr = add(ops, PK_TRTRI, (int)n * r, tb, r, tr);
     int opG = -1, opH = -1;
     if (n > 1) {
       PGemm g = gemm(w.G, b, bb, B, B, (int)(n - 1), 0.0, 0, 0);
@@ -723,8 +755,8 @@ struct Builder {
     if (a > 0) {
       trtris.push_back(PTrtri{e.tip, w.LtInv, a, a * a, Aa, na, 1});
       const int tt = (int)trtris.size() - 1;
-      int t2 = add(ops, PK_TINV, na, tt, 0, 0.6, fac);
-      for (int r = 1; r < na; ++r) t2 = add(ops, PK_TRTRI, r, tt, r, 1.2 + 0.5 * r, t2);
+      int t2 = add(ops, PK_TINV, na, tt, 0, fac);
+      for (int r = 1; r < na; ++r) t2 = add(ops, PK_TRTRI, r, tt, r, t2);
       PGemm g = gemm(e.tip, a, 0, Aa, Aa, 1, 0.0, 1, 1);
       g.t[0] = term(w.LtInv, a, 0, OP_T, TRI_UPPER, w.LtInv, a, 0, OP_N, TRI_LOWER, Aa, 1.0);
       g.nterms = 1;
@@ -766,44 +798,6 @@ struct Builder {
 
 }  // namespace
 
-namespace {
-
-// Lane simulation: matrices largest first, each to the least-loaded of W lanes of
-// C = G / W CTAs; an op of `items` items of time tau takes ceil(items / C) tau.
-struct LaneSched {
-  std::vector<int> lane_of;        // per matrix
-  std::vector<double> start_of;    // per matrix (lane time)
-  double makespan = 0.0;
-};
-
-double op_dur(const HOp& h, int C) { return (double)((h.op.nitems + C - 1) / C) * h.tau; }
-
-LaneSched schedule_lanes(const std::vector<std::vector<HOp>>& prog, int G, int W) {
-  const int cnt = (int)prog.size();
-  const int C = std::max(1, G / W);
-  std::vector<double> dur(cnt, 0.0);
-  for (int m = 0; m < cnt; ++m)
-    for (const HOp& h : prog[m]) dur[m] += op_dur(h, C);
-  std::vector<int> order(cnt);
-  for (int m = 0; m < cnt; ++m) order[m] = m;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return dur[x] > dur[y]; });
-  LaneSched ls;
-  ls.lane_of.assign(cnt, 0);
-  ls.start_of.assign(cnt, 0.0);
-  std::vector<double> load(W, 0.0);
-  for (int m : order) {
-    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    ls.lane_of[m] = l;
-    ls.start_of[m] = load[l];
-    load[l] += dur[m];
-  }
-  ls.makespan = *std::max_element(load.begin(), load.end());
-  return ls;
-}
-
-constexpr size_t kCounterHeader = 64;  // ints: cursor, error, padding
-
-}  // namespace
 
 typedef void (*PKernel)(PDev);
 
@@ -830,13 +824,16 @@ using namespace bta;
 struct bta_plan_s {
   int device = -1;
   int count = 0;
-  int grid = 0, lanes = 0, R = 1, ctas_per_sm = 0;
-  int nops = 0;
+  int grid = 0, small_items = 0, R = 1, ctas_per_sm = 0;
+  int nops = 0, ninit = 0;
   long long nitems = 0;
-  double flops = 0.0, makespan_est = 0.0;
-  void* desc = nullptr;       // descriptor tables
-  void* counters = nullptr;   // cursor, error, taken, done, info
+  double flops = 0.0;
+  void* desc = nullptr;      // descriptor tables and the seed image of the counters
+  void* counters = nullptr;  // header, taken, done, sat, two queues, info
   size_t counter_bytes = 0;
+  const int* seed_hdr = nullptr;    // device: header values of a fresh run
+  const int* seed_queue[2] = {nullptr, nullptr};  // device: initially ready operations
+  int seed_len[2] = {0, 0};
   const void* kernel = nullptr;
   PDev d{};
 };
@@ -856,7 +853,7 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   *out = nullptr;
   bta_plan_params prm{};
   if (params) prm = *params;
-  if (prm.ctas_per_sm < 0 || prm.ctas_per_sm > 16 || prm.lanes < 0 || prm.lanes > 65536 ||
+  if (prm.ctas_per_sm < 0 || prm.ctas_per_sm > 16 || prm.small_items < 0 ||
       prm.rows_per_item < 0 || prm.rows_per_item > kPMaxR)
     return -3;
   for (int64_t k = 0; k < count; ++k) {
@@ -870,139 +867,155 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
     if (e.logdet_out && ((uintptr_t)e.logdet_out % 8)) return -2;
   }
   const int R = prm.rows_per_item ? prm.rows_per_item : 1;
+  const int small = prm.small_items ? prm.small_items : 32;
   const PKernel kern = pick_kernel(R);
   int per_sm = 0, sms = 0;
   cudaError_t ce = plan_occupancy(kern, &per_sm, &sms);
   if (ce != cudaSuccess) return (int)ce;
   if (per_sm < 1 || sms < 1) return (int)cudaErrorInvalidConfiguration;
-  const int occ = prm.ctas_per_sm ? std::min(prm.ctas_per_sm, per_sm) : per_sm;
+  // Four CTAs per SM by default: enough warps to keep the FP64 pipe busy, while
+  // more resident CTAs than ready items only add idle polling (measured on the
+  // 64-matrix batch: 2.76 s at 4 per SM, 3.12 s at 8, 3.07 s at 2).
+  const int occ = std::min(prm.ctas_per_sm ? prm.ctas_per_sm : 4, per_sm);
   const int G = occ * sms;
-  Builder bld;
-  bld.R = R;
-  std::vector<std::vector<HOp>> prog(count);
+  // Matrices largest first: their operations come first in the tables and their
+  // first operations first in the initial queue.
+  std::vector<double> fl(count);
   double flops = 0.0;
   for (int64_t k = 0; k < count; ++k) {
-    bld.add_matrix((int)k, entries[k], prog[k]);
     const double B = (double)entries[k].b, A = (double)entries[k].a, n = (double)entries[k].n;
-    flops += n * B * B * B / 3 + (n - 1) * 2 * B * B * B + n * A * B * B + (n - 1) * 2 * A * B * B +
-             n * A * A * B + A * A * A / 3 + 2 * A * A * A / 3 + n * 2 * B * B * B / 3 +
-             (n - 1) * 4 * B * B * B + n * (2 * A * B * B + 2 * A * A * B) + (n - 1) * 4 * A * B * B;
+    fl[k] = n * B * B * B / 3 + (n - 1) * 2 * B * B * B + n * A * B * B + (n - 1) * 2 * A * B * B +
+            n * A * A * B + A * A * A / 3 + 2 * A * A * A / 3 + n * 2 * B * B * B / 3 +
+            (n - 1) * 4 * B * B * B + n * (2 * A * B * B + 2 * A * A * B) + (n - 1) * 4 * A * B * B;
+    flops += fl[k];
   }
-  // Lanes: the given count, else the one with the shortest simulated makespan.
-  int W = prm.lanes;
-  LaneSched ls;
-  if (W > 0) {
-    W = (int)std::min<int64_t>(W, count);
-    ls = schedule_lanes(prog, G, W);
-  } else {
-    double best = 0.0;
-    const int wmax = (int)std::min<int64_t>(count, G);
-    for (int w = 1; w <= wmax; w = std::max(w + 1, w * 5 / 4)) {
-      LaneSched c = schedule_lanes(prog, G, w);
-      if (W == 0 || c.makespan < best * 0.999) {
-        best = c.makespan;
-        W = w;
-        ls = c;
-      }
-    }
-  }
-  // Global order: simulated start time, then lane, then program position.
-  struct Key {
-    double start;
-    int lane, mat, local;
-  };
-  std::vector<Key> keys;
-  const int C = std::max(1, G / W);
-  for (int64_t m = 0; m < count; ++m) {
-    double t = ls.start_of[m];
-    for (const HOp& h : prog[m]) {
-      keys.push_back(Key{t, ls.lane_of[m], (int)m, h.local});
-      t += op_dur(h, C);
-    }
-  }
-  std::stable_sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
-    if (x.start != y.start) return x.start < y.start;
-    if (x.lane != y.lane) return x.lane < y.lane;
-    return x.local < y.local;
-  });
-  std::vector<std::vector<int>> pos(count);
-  for (int64_t m = 0; m < count; ++m) pos[m].assign(prog[m].size(), -1);
-  for (size_t q = 0; q < keys.size(); ++q) pos[keys[q].mat][keys[q].local] = (int)q;
-  std::vector<POp> ops(keys.size());
+  std::vector<int64_t> order(count);
+  for (int64_t k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return fl[x] > fl[y]; });
+  Builder bld;
+  bld.R = R;
+  std::vector<POp> ops;
+  std::vector<std::vector<int>> succ;
+  std::vector<int> init[2];
   long long nitems = 0;
-  for (size_t q = 0; q < keys.size(); ++q) {
-    POp o = prog[keys[q].mat][keys[q].local].op;
-    for (int j = 0; j < 4; ++j) {
-      if (o.dep[j] < 0) continue;
-      o.dep[j] = pos[keys[q].mat][o.dep[j]];
-      if (o.dep[j] < 0 || o.dep[j] >= (int)q) return (int)cudaErrorInvalidValue;  // not earlier
+  for (int64_t m : order) {
+    std::vector<HOp> prog;
+    bld.add_matrix((int)m, entries[m], prog);
+    const int base = (int)ops.size();
+    if ((size_t)base + prog.size() > (size_t)0x3fffffff) return -1;
+    succ.resize(base + prog.size());
+    for (const HOp& h : prog) {
+      POp o = h.op;
+      int deps[4], nd = 0;
+      for (int j = 0; j < 4; ++j) {
+        const int dl = h.dep[j];
+        if (dl < 0) continue;
+        if (dl >= h.local) return (int)cudaErrorInvalidValue;  // must be an earlier operation
+        bool dup = false;
+        for (int q = 0; q < nd; ++q) dup = dup || deps[q] == dl;
+        if (!dup) deps[nd++] = dl;
+      }
+      o.ndeps = nd;
+      o.prio = o.nitems <= small ? 0 : 1;
+      const int gi = base + h.local;
+      for (int q = 0; q < nd; ++q) succ[base + deps[q]].push_back(gi);
+      if (nd == 0) init[o.prio].push_back(gi);
+      nitems += o.nitems;
+      ops.push_back(o);
     }
-    // Descriptor indices are global already (the builder's tables span the batch).
-    ops[q] = o;
-    nitems += o.nitems;
   }
-  if (ops.size() > (size_t)0x7fffffff || nitems > (1ll << 40)) return -1;
+  std::vector<int> succ_flat;
+  for (size_t q = 0; q < ops.size(); ++q) {
+    ops[q].succ_off = (int)succ_flat.size();
+    ops[q].nsucc = (int)succ[q].size();
+    succ_flat.insert(succ_flat.end(), succ[q].begin(), succ[q].end());
+  }
+  const int nops = (int)ops.size();
+  // Seed image of a run: header (queue tails = initially ready counts) and the
+  // initial queue entries (op + 1).
+  std::vector<int> seed_hdr(kCounterHeader, 0);
+  seed_hdr[3] = (int)init[0].size();
+  seed_hdr[5] = (int)init[1].size();
+  std::vector<int> seed_q[2];
+  for (int q = 0; q < 2; ++q)
+    for (int v : init[q]) seed_q[q].push_back(v + 1);
 
   bta_plan_s* P = new (std::nothrow) bta_plan_s;
   if (!P) return (int)cudaErrorMemoryAllocation;
   cudaGetDevice(&P->device);
   P->count = (int)count;
   P->grid = G;
-  P->lanes = W;
-  P->R = bld.R;
+  P->small_items = small;
+  P->R = R;
   P->kernel = (const void*)kern;
   P->ctas_per_sm = occ;
-  P->nops = (int)ops.size();
+  P->nops = nops;
+  P->ninit = (int)(init[0].size() + init[1].size());
   P->nitems = nitems;
   P->flops = flops;
-  P->makespan_est = ls.makespan;
-  const size_t b_ops = align256(ops.size() * sizeof(POp));
-  const size_t b_steps = align256(bld.steps.size() * sizeof(PStep) + 1);
-  const size_t b_gemms = align256(bld.gemms.size() * sizeof(PGemm) + 1);
-  const size_t b_trtris = align256(bld.trtris.size() * sizeof(PTrtri) + 1);
-  const size_t b_mats = align256(bld.mats.size() * sizeof(PMat) + 1);
-  const size_t total = b_ops + b_steps + b_gemms + b_trtris + b_mats;
-  P->counter_bytes = align256((kCounterHeader + 2 * ops.size()) * sizeof(int)) +
+  struct Part {
+    const void* src;
+    size_t bytes;
+  };
+  const Part parts[] = {{ops.data(), ops.size() * sizeof(POp)},
+                        {succ_flat.data(), succ_flat.size() * sizeof(int)},
+                        {bld.steps.data(), bld.steps.size() * sizeof(PStep)},
+                        {bld.gemms.data(), bld.gemms.size() * sizeof(PGemm)},
+                        {bld.trtris.data(), bld.trtris.size() * sizeof(PTrtri)},
+                        {bld.mats.data(), bld.mats.size() * sizeof(PMat)},
+                        {seed_hdr.data(), seed_hdr.size() * sizeof(int)},
+                        {seed_q[0].data(), seed_q[0].size() * sizeof(int)},
+                        {seed_q[1].data(), seed_q[1].size() * sizeof(int)}};
+  constexpr int kParts = sizeof(parts) / sizeof(parts[0]);
+  size_t total = 0, at[kParts];
+  for (int q = 0; q < kParts; ++q) {
+    at[q] = total;
+    total += align256(parts[q].bytes + 1);
+  }
+  const size_t n_int = (size_t)nops;
+  P->counter_bytes = align256((kCounterHeader + 5 * n_int) * sizeof(int)) +
                      align256(count * sizeof(unsigned long long));
   ce = cudaMalloc(&P->desc, total);
   if (ce == cudaSuccess) ce = cudaMalloc(&P->counters, P->counter_bytes);
+  if (ce == cudaSuccess) {
+    std::vector<char> host(total, 0);
+    for (int q = 0; q < kParts; ++q)
+      if (parts[q].bytes) memcpy(host.data() + at[q], parts[q].src, parts[q].bytes);
+    ce = cudaMemcpy(P->desc, host.data(), total, cudaMemcpyHostToDevice);
+  }
   if (ce != cudaSuccess) {
     if (P->desc) cudaFree(P->desc);
+    if (P->counters) cudaFree(P->counters);
     delete P;
     return (int)ce;
   }
-  std::vector<char> host(total, 0);
-  size_t off = 0;
-  auto put = [&](const void* src, size_t bytes, size_t span) {
-    if (bytes) memcpy(host.data() + off, src, bytes);
-    const size_t at = off;
-    off += span;
-    return (char*)P->desc + at;
-  };
-  P->d.ops = (const POp*)put(ops.data(), ops.size() * sizeof(POp), b_ops);
-  P->d.steps = (const PStep*)put(bld.steps.data(), bld.steps.size() * sizeof(PStep), b_steps);
-  P->d.gemms = (const PGemm*)put(bld.gemms.data(), bld.gemms.size() * sizeof(PGemm), b_gemms);
-  P->d.trtris = (const PTrtri*)put(bld.trtris.data(), bld.trtris.size() * sizeof(PTrtri), b_trtris);
-  P->d.mats = (const PMat*)put(bld.mats.data(), bld.mats.size() * sizeof(PMat), b_mats);
-  ce = cudaMemcpy(P->desc, host.data(), total, cudaMemcpyHostToDevice);
-  if (ce != cudaSuccess) {
-    cudaFree(P->desc);
-    cudaFree(P->counters);
-    delete P;
-    return (int)ce;
-  }
-  int* cbase = (int*)P->counters;
-  P->d.nops = P->nops;
-  P->d.cursor = cbase;
-  P->d.error = cbase + 1;
-  P->d.taken = cbase + kCounterHeader;
-  P->d.done = P->d.taken + ops.size();
+  char* D = (char*)P->desc;
+  P->d.ops = (const POp*)(D + at[0]);
+  P->d.succ = (const int*)(D + at[1]);
+  P->d.steps = (const PStep*)(D + at[2]);
+  P->d.gemms = (const PGemm*)(D + at[3]);
+  P->d.trtris = (const PTrtri*)(D + at[4]);
+  P->d.mats = (const PMat*)(D + at[5]);
+  P->seed_hdr = (const int*)(D + at[6]);
+  P->seed_queue[0] = (const int*)(D + at[7]);
+  P->seed_queue[1] = (const int*)(D + at[8]);
+  P->seed_len[0] = (int)seed_q[0].size();
+  P->seed_len[1] = (int)seed_q[1].size();
+  int* c = (int*)P->counters;
+  P->d.nops = nops;
+  P->d.hdr = c;
+  P->d.taken = c + kCounterHeader;
+  P->d.done = P->d.taken + n_int;
+  P->d.sat = P->d.done + n_int;
+  P->d.queue = P->d.sat + n_int;
   P->d.info = (unsigned long long*)((char*)P->counters +
-                                    align256((kCounterHeader + 2 * ops.size()) * sizeof(int)));
-  P->d.max_polls = 1u << 22;  // with 256 ns sleeps: a few seconds per wait
+                                    align256((kCounterHeader + 5 * n_int) * sizeof(int)));
+  P->d.max_polls = 1u << 22;  // polls (128 ns sleeps) without any operation completing
   *out = P;
   return 0;
 }
+
+static inline size_t n_ops(const bta_plan_s* P) { return (size_t)P->nops; }
 
 int bta_plan_run(bta_plan plan, bta_stream_t stream) {
   bta_plan_s* P = plan;
@@ -1013,6 +1026,12 @@ int bta_plan_run(bta_plan plan, bta_stream_t stream) {
   if (dev != P->device) return -1;
   const cudaStream_t s = (cudaStream_t)stream;
   e = cudaMemsetAsync(P->counters, 0, P->counter_bytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->d.hdr, P->seed_hdr, kCounterHeader * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+    if (P->seed_len[q])
+      e = cudaMemcpyAsync(P->d.queue + q * n_ops(P), P->seed_queue[q], P->seed_len[q] * sizeof(int),
+                          cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return (int)e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)P->grid);
@@ -1034,7 +1053,7 @@ int bta_plan_status(bta_plan plan, int* timed_out, int64_t* info, bta_stream_t s
   if (!P) return -1;
   const cudaStream_t s = (cudaStream_t)stream;
   int err = 0;
-  cudaError_t e = cudaMemcpyAsync(&err, P->d.error, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(&err, P->d.hdr, sizeof(int), cudaMemcpyDeviceToHost, s);
   std::vector<unsigned long long> inf(P->count, 0);
   if (e == cudaSuccess && info)
     e = cudaMemcpyAsync(inf.data(), P->d.info, P->count * sizeof(unsigned long long),
@@ -1051,8 +1070,8 @@ int bta_plan_describe(bta_plan plan, int64_t* out, int nout) {
   bta_plan_s* P = plan;
   if (!P) return -1;
   if (!out || nout < 1) return -2;
-  const int64_t v[8] = {P->grid, P->ctas_per_sm, P->lanes, P->R, P->nops, P->nitems,
-                        (int64_t)P->flops, (int64_t)P->makespan_est};
+  const int64_t v[8] = {P->grid, P->ctas_per_sm, P->small_items, P->R, P->nops, P->nitems,
+                        (int64_t)P->flops, P->ninit};
   for (int q = 0; q < nout && q < 8; ++q) out[q] = v[q];
   return 0;
 }
