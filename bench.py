@@ -49,9 +49,17 @@ WORKLOADS = {
     # small cases with the same block shapes, for profiler captures (under 1 GB on the device)
     "n48_b1024_a8": dict(n=48, b=1024, a=8, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
     "n8_b2048_a16": dict(n=8, b=2048, a=16, shift=gen.SHIFT_1_001, shift_name="1.001 x row sum"),
+    # the block shape of the paper's weak-scaling dataset (4) at one process (Section 5.2, 5.4)
+    "n90_b2865_a4": dict(n=90, b=2865, a=4, shift=gen.SHIFT_1_01, shift_name="1.01 x row sum"),
 }
+# The paper's one single-GPU factorization time: block-sequential POBTAF on dataset (4) at one
+# process, n=90, b=2865, a=4, FP64, on one GH200 (Section 5.4). Context, not a target.
+PAPER_POBTAF_GH200_MS = 2510.0
 NRHS = 4
 BATCH_WORKLOAD = "batch64_n20-200_b128-512_a2-8"
+# a 16-matrix sample of the same kind, about 1 GB on the device: the persistent
+# kernel alone, for profiler captures
+BATCH_SMALL = "batch16_n20-40_b128-512_a2-8"
 
 
 # Algorithmic FP64 flops (LAPACK counts of the method itself).
@@ -481,6 +489,41 @@ def _batch_oracle_check(raw, W, logdets, sample):
             "max_logdet_rel_err_vs_oracle": float(f"{ld_err:.3e}")}
 
 
+def run_batch_small(args):
+    """The persistent batched kernel on the 16-matrix sample (default plan
+    parameters): W warm-up and K timed launches, one JSON line."""
+    import torch
+    from paper_2503_17528_gb300.batched import PersistentBatch
+    rng = np.random.default_rng(77)
+    shapes = [(int(rng.integers(20, 41)), int(rng.choice([128, 256, 512])), int(rng.choice([2, 4, 8])))
+              for _ in range(16)]
+    raw = [gen.make_bta(n, b, a, seed=900 + k, shift=gen.SHIFT_1_01) for k, (n, b, a) in enumerate(shapes)]
+    dev = torch.device("cuda", 0)
+    P = [tuple(torch.from_numpy(x).to(dev) for x in m) for m in raw]
+    W = [tuple(x.clone() for x in m) for m in P]
+    pb = PersistentBatch(W)
+
+    def step():
+        for w, p in zip(W, P):
+            for x, y in zip(w, p):
+                if x.numel():
+                    x.copy_(y, non_blocking=True)
+        pb.run()
+
+    ms = _timed_steps(step, args.steps, args.warmup, dev)
+    to, info = pb.status()
+    fl = sum(flops_factor(n, b, a) + flops_selinv(n, b, a) for n, b, a in shapes)
+    print(json.dumps({"metric": "BTA persistent batched factor+logdet+selinv ms/batch", "value": round(ms, 3),
+                      "unit": "ms/batch", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": BATCH_SMALL, "shapes": shapes, "plan": pb.describe(),
+                                 "steps_include": "device reset copy + one persistent launch"},
+                      "tflops": round(fl / (ms * 1e-3) / 1e12, 4), "timed_out": to,
+                      "failed_matrices": sum(1 for v in info if v)}), flush=True)
+    pb.close()
+    return 0
+
+
 def run_batch(args, rank=0, world=1, local_rank=0):
     """The batched workload as its own bench line: each rank runs its shard of the
     64 matrices (largest-first bin-pack on algorithmic flops, no data-path
@@ -643,6 +686,62 @@ def run_modes(args, bta, lib, step, step_seq, W, ld_out, base_ms, dev, ref_input
             "max_block_rel_err_vs_" + args.precision: {k: float(f"{v:.3e}") for k, v in errs.items()},
             "parts": P, "load_balance_top": 1.8}
     return res
+
+
+def run_context(dev, steps, peak_tf):
+    """The dataset-4 block shape (n=90, b=2865, a=4: a ragged 17-row last tile)
+    beside the paper's 2.51 s POBTAF on GH200: factor alone (POBTAF) and the
+    whole path (factor + log det + solve + selinv), in FP64 and in the Ozaki
+    mode, each after one warm-up, with the Ozaki result's largest per-block
+    error against the FP64 one."""
+    import torch
+    import paper_2503_17528_gb300 as bta
+    w = WORKLOADS["n90_b2865_a4"]
+    n, b, a = w["n"], w["b"], w["a"]
+    arrays = make_workload(w, seed=0)
+    P = [torch.from_numpy(x).to(dev) for x in arrays]
+    del arrays
+    W = [torch.empty_like(x) for x in P]
+    ld = torch.empty((), dtype=torch.float64, device=dev)
+
+    def reset():
+        for dst, src in zip(W, P):
+            dst.copy_(src, non_blocking=True)
+
+    def factor_only():
+        reset()
+        bta.factor(*W[:4])
+
+    def whole():
+        reset()
+        bta.factor_selinv_all(*W[:4], rhs=W[4], logdet_out=ld)
+
+    def copy_ms():
+        return _timed_steps(reset, steps, 1, dev)
+
+    out = {"workload": "n90_b2865_a4", "n": n, "b": b, "a": a,
+           "paper_pobtaf_gh200_ms": PAPER_POBTAF_GH200_MS,
+           "note": "paper: block-sequential POBTAF, dataset (4) at P=1, FP64, 1 GH200 (67 TFLOP/s FP64 "
+                   "tensor); here synthetic blocks of the same shape; times exclude the reset copy"}
+    reset_ms = copy_ms()
+    res = {}
+    for prec in ("fp64", "ozaki"):
+        bta.set_precision(prec)
+        f_ms = _timed_steps(factor_only, steps, 1, dev) - reset_ms
+        a_ms = _timed_steps(whole, steps, 1, dev) - reset_ms
+        res[prec] = {"factor_ms": round(f_ms, 1), "factor_tflops": round(flops_factor(n, b, a) / (f_ms * 1e-3) / 1e12, 4),
+                     "factor_selinv_logdet_solve_ms": round(a_ms, 1),
+                     "factor_vs_paper_gh200": round(PAPER_POBTAF_GH200_MS / f_ms, 3)}
+        if prec == "fp64":
+            ref = [x.clone() for x in W[:4]]
+        else:
+            res[prec]["max_block_rel_err_vs_fp64"] = float(f"{max(blockerr(x, y) for x, y in zip(W[:4], ref) if y.numel()):.3e}")
+    bta.set_precision("fp64")
+    res["fp64"]["factor_frac_of_fp64_peak"] = round(res["fp64"]["factor_tflops"] / peak_tf, 4)
+    out.update(res)
+    del P, W
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -836,6 +935,9 @@ def run_ours(args, w, rank, world, local_rank):
     # The main workload's device buffers are no longer needed.
     del P, W
     torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.context:
+        _log("context workload n90_b2865_a4")
+        out["context"] = run_context(dev, 1, peak_tf)
     if rank == 0 and world == 1 and not args.no_batch:
         _log("batched form")
         batched = batch_measure(max(1, min(args.steps, args.mode_steps)), max(1, min(args.warmup, args.mode_warmup)),
@@ -860,7 +962,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default="n256_b2048_a16")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, BATCH_SMALL], default="n256_b2048_a16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
@@ -872,6 +974,8 @@ def main():
     ap.add_argument("--mode-steps", type=int, default=3, help="timed steps per extra precision mode")
     ap.add_argument("--mode-warmup", type=int, default=1, help="warm-up steps per extra precision mode")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form sub-record")
+    ap.add_argument("--no-context", dest="context", action="store_false",
+                    help="skip the dataset-4-shaped context record (n=90, b=2865, a=4)")
     ap.add_argument("--batch-oracle-sample", type=int, default=4,
                     help="matrices of the batched result checked against the oracle")
     ap.add_argument("--cpu-target-s", type=float, default=10.0)
@@ -881,8 +985,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload == BATCH_WORKLOAD and args.impl == "reference":
+    if args.workload in (BATCH_WORKLOAD, BATCH_SMALL) and args.impl == "reference":
         return 0
+    if args.workload == BATCH_SMALL:
+        return run_batch_small(args)
     if args.impl == "reference":
         return run_reference(args, WORKLOADS[args.workload], rank, world)
     if world > 1:
