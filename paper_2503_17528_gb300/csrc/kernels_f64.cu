@@ -572,6 +572,13 @@ __device__ int g_wait_error;
 // contiguous range of u, so its tiles split evenly over the CTAs.
 // ---------------------------------------------------------------------------
 constexpr int kStepThreads = 256;
+// Resident CTAs per SM of the step kernel (its register budget and grid size):
+// 60 registers, no spills; 4 per SM factored n=32, b=2048, a=16 in 648 ms
+// against 651 ms at 3 and 660 ms at 2 (bit-identical results).
+#ifndef BTA_STEP_CTAS_PER_SM
+#define BTA_STEP_CTAS_PER_SM 4
+#endif
+constexpr int kStepCtasPerSm = BTA_STEP_CTAS_PER_SM;
 
 struct StepArgs {
   double* D0;   // A_ii (b x b): L_ii on return, strict upper triangle zeroed
@@ -688,7 +695,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-__global__ void __launch_bounds__(kStepThreads, 2) factor_step_kernel(StepArgs p) {
+__global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) factor_step_kernel(StepArgs p) {
   __shared__ double Pb[2][T][T + 1];  // L(r, k), double-buffered
   __shared__ double Qb[2][T][T + 1];  // L(c, k)
   __shared__ double rd[T];
@@ -888,7 +895,7 @@ static int step_grid() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_step_kernel, kStepThreads, 0);
     // Several CTAs per SM: one CTA's loads, stores and barriers overlap the
     // others' DMMA work on the SM's FP64 pipe.
-    const int g = std::min(per, 2) * sms;
+    const int g = std::min(per, kStepCtasPerSm) * sms;
     return (long long)(g > 0 ? g : -1);
   });
 }

@@ -8,7 +8,7 @@ step k, then finalize it), 2(k) (update column k+2) and 3(k) (update columns
 finalized tiles: tile (r, c) is final once the row counter pdone[r] > c (the
 bulk phase 3(k) instead waits once for the whole of column k). This
 replay checks, for block counts, arrowheads, the last block, Schur updates on
-or off and grid sizes from 2 to 304, that (1) the operations are exactly the tile
+or off and grid sizes from 2 to 608 (2 to 4 CTAs per SM on 152 SMs), that (1) the operations are exactly the tile
 Cholesky's (every update U(r, c, k), k < c, once; every finalization once),
 (2) each tile sees its updates in k order and is finalized after all of them,
 and (3) the CTAs, each in its own order, always complete: flags only grow, so
@@ -89,7 +89,7 @@ def _replay(E, items):
 @pytest.mark.parametrize("nt,na,nxt,schur", list(itertools.product([1, 2, 3, 5, 8, 33, 64], [0, 1, 2],
                                                                     [0, 1], [0, 1])))
 def test_factor_step_schedule_is_complete_and_deadlock_free(nt, na, nxt, schur):
-    for G in (2, 3, 7, 304):
+    for G in (2, 3, 7, 304, 456, 608):
         E, Ecol, items = _schedule(nt, na, nxt, schur, G)
         ops = [("U",) + it[1:] if it[0] == "B" else it for lst in items for it in lst]
         want = {("U", r, c, k) for c in range(Ecol) for r in range(c, E) for k in range(min(c, nt))}
