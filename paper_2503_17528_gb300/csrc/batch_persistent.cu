@@ -342,50 +342,89 @@ __device__ void item_gemm(const PGemm& g, int item, PSmem<MAXR>& sm) {
   double acc[MAXR][2][2][2];
 #pragma unroll
   for (int q = 0; q < MAXR; ++q) zero_acc(acc[q]);
-  for (int ti = 0; ti < g.nterms; ++ti) {
+  // The k-chunks of every term, in order; each chunk's operands are fetched into
+  // registers one chunk ahead (ld.global.cg), so the loads of chunk c+1 are in
+  // flight while chunk c's DMMAs run.
+  // k range of term ti (structural zeros of triangular operands skipped; nr == 1
+  // whenever op(A) is triangular).
+  auto krange = [&](int ti, int& kb, int& ke) {
     const PTerm& t = g.t[ti];
-    const double* A = t.A + (int64_t)z * t.sA;
-    const double* B = t.B + (int64_t)z * t.sB;
-    int kb = 0, ke = t.K;
-    if (t.triA == TRI_LOWER) ke = min(ke, m0 + T);  // nr == 1 whenever op(A) is triangular
+    kb = 0;
+    ke = t.K;
+    if (t.triA == TRI_LOWER) ke = min(ke, m0 + T);
     if (t.triA == TRI_UPPER) kb = max(kb, m0);
     if (t.triB == TRI_LOWER) kb = max(kb, n0);
     if (t.triB == TRI_UPPER) ke = min(ke, n0 + T);
-    for (int k0 = kb; k0 < ke; k0 += T) {
-      const int kl = min(T, ke - k0);
-      if (t.opB == OP_N) {
-        for (int e = tid; e < T * T; e += kPThreads) {
-          const int kk = e / T, j = e % T;
-          sm.B[j][kk] = (kk < kl && n0 + j < g.N) ? ldcg(B + (int64_t)(k0 + kk) * t.ldb + n0 + j) : 0.0;
-        }
-      } else {
-        for (int e = tid; e < T * T; e += kPThreads) {
-          const int j = e / T, kk = e % T;
-          sm.B[j][kk] = (kk < kl && n0 + j < g.N) ? ldcg(B + (int64_t)(n0 + j) * t.ldb + k0 + kk) : 0.0;
-        }
-      }
-      for (int q = 0; q < nr; ++q) {
-        const int mq = m0 + q * T;
-        if (t.opA == OP_N) {
-          for (int e = tid; e < T * T; e += kPThreads) {
-            const int i = e / T, kk = e % T;
-            const double v = (kk < kl && mq + i < g.M) ? ldcg(A + (int64_t)(mq + i) * t.lda + k0 + kk) : 0.0;
-            sm.A[q][i][kk] = scale_by(v, t.alpha);
-          }
-        } else {
-          for (int e = tid; e < T * T; e += kPThreads) {
-            const int kk = e / T, i = e % T;
-            const double v = (kk < kl && mq + i < g.M) ? ldcg(A + (int64_t)(k0 + kk) * t.lda + mq + i) : 0.0;
-            sm.A[q][i][kk] = scale_by(v, t.alpha);
-          }
-        }
-      }
-      __syncthreads();
+  };
+  int kb0 = 0, ke0 = 0, kb1 = 0, ke1 = 0;
+  if (g.nterms > 0) krange(0, kb0, ke0);
+  if (g.nterms > 1) krange(1, kb1, ke1);
+  const int nch0 = ke0 > kb0 ? (ke0 - kb0 + T - 1) / T : 0;
+  const int nch1 = ke1 > kb1 ? (ke1 - kb1 + T - 1) / T : 0;
+  const int total = nch0 + nch1;
+  constexpr int PER = T * T / kPThreads;  // elements of a 32 x 32 chunk per thread
+  double ra[MAXR][PER], rb[PER];
+  auto fetch = [&](int ci) {
+    const int ti = ci < nch0 ? 0 : 1;
+    const PTerm& t = g.t[ti];
+    const int k0 = ti ? kb1 + (ci - nch0) * T : kb0 + ci * T, kl = min(T, (ti ? ke1 : ke0) - k0);
+    const double* A = t.A + (int64_t)z * t.sA;
+    const double* B = t.B + (int64_t)z * t.sB;
 #pragma unroll
-      for (int q = 0; q < MAXR; ++q)
-        if (q < nr) mma_chunk(acc[q], sm.A[q], sm.B, kl);
-      __syncthreads();
+    for (int x = 0; x < PER; ++x) {
+      const int e = tid + x * kPThreads;
+      if (t.opB == OP_N) {
+        const int kk = e / T, jj = e % T;
+        rb[x] = (kk < kl && n0 + jj < g.N) ? ldcg(B + (int64_t)(k0 + kk) * t.ldb + n0 + jj) : 0.0;
+      } else {
+        const int jj = e / T, kk = e % T;
+        rb[x] = (kk < kl && n0 + jj < g.N) ? ldcg(B + (int64_t)(n0 + jj) * t.ldb + k0 + kk) : 0.0;
+      }
     }
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      if (q >= nr) break;
+      const int mq = m0 + q * T;
+#pragma unroll
+      for (int x = 0; x < PER; ++x) {
+        const int e = tid + x * kPThreads;
+        if (t.opA == OP_N) {
+          const int ii = e / T, kk = e % T;
+          ra[q][x] = (kk < kl && mq + ii < g.M) ? ldcg(A + (int64_t)(mq + ii) * t.lda + k0 + kk) : 0.0;
+        } else {
+          const int kk = e / T, ii = e % T;
+          ra[q][x] = (kk < kl && mq + ii < g.M) ? ldcg(A + (int64_t)(k0 + kk) * t.lda + mq + ii) : 0.0;
+        }
+      }
+    }
+  };
+  if (total > 0) fetch(0);
+  for (int ci = 0; ci < total; ++ci) {
+    const int ti = ci < nch0 ? 0 : 1;
+    const PTerm& t = g.t[ti];
+    const int k0 = ti ? kb1 + (ci - nch0) * T : kb0 + ci * T, kl = min(T, (ti ? ke1 : ke0) - k0);
+#pragma unroll
+    for (int x = 0; x < PER; ++x) {
+      const int e = tid + x * kPThreads;
+      if (t.opB == OP_N) sm.B[e % T][e / T] = rb[x];
+      else sm.B[e / T][e % T] = rb[x];
+    }
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      if (q >= nr) break;
+#pragma unroll
+      for (int x = 0; x < PER; ++x) {
+        const int e = tid + x * kPThreads;
+        if (t.opA == OP_N) sm.A[q][e / T][e % T] = scale_by(ra[q][x], t.alpha);
+        else sm.A[q][e % T][e / T] = scale_by(ra[q][x], t.alpha);
+      }
+    }
+    __syncthreads();
+    if (ci + 1 < total) fetch(ci + 1);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q)
+      if (q < nr) mma_chunk(acc[q], sm.A[q], sm.B, kl);
+    __syncthreads();
   }
   double* C = g.C + (int64_t)z * g.sC;
   if (!g.mirror) {
@@ -801,10 +840,11 @@ struct Builder {
 
 typedef void (*PKernel)(PDev);
 
-// Two builds of the kernel: registers for 4 CTAs per SM and items of up to two
-// tile rows, or for 8 CTAs per SM and one tile row.
+// Two builds of the kernel, both with the register budget of 4 CTAs per SM (the
+// operands of the next k-chunk are held in registers): items of one tile row,
+// or of up to two.
 static PKernel pick_kernel(int R) {
-  return R > 1 ? (PKernel)persistent_kernel<4, 2> : (PKernel)persistent_kernel<8, 1>;
+  return R > 1 ? (PKernel)persistent_kernel<4, 2> : (PKernel)persistent_kernel<4, 1>;
 }
 
 static cudaError_t plan_occupancy(PKernel k, int* per_sm, int* sms) {

@@ -86,8 +86,8 @@ def tune(mats, pristine, policies=None, streams=STREAMS, reps=2, save=True):
 
 
 # Candidates of the persistent kernel: (CTAs per SM, priority threshold in items,
-# tile rows per item). Two tile rows need the 4-CTAs-per-SM register budget.
-PERSISTENT_CANDIDATES = tuple((c, w, r) for r in (1, 2) for c in ((2, 3, 4, 6) if r == 1 else (2, 4))
+# tile rows per item). Both builds of the kernel hold at most 4 CTAs per SM.
+PERSISTENT_CANDIDATES = tuple((c, w, r) for r in (1, 2) for c in ((2, 3, 4) if r == 1 else (2, 4))
                               for w in (8, 32, 128))
 
 
