@@ -102,3 +102,38 @@ def test_one_call_forms_check_arguments_before_the_gpu(lib):
     t = ctypes.c_int(0)
     assert lib.bta_wait_selftest(0, ctypes.byref(t)) == -1
     assert lib.bta_wait_selftest(10, None) == -2
+
+
+def test_persistent_plan_checks_arguments_before_the_gpu(lib):
+    """bta_plan_* reject bad arguments without touching the GPU, and the per-matrix
+    workspace holds L^{-1}, G, H, L_nn^{-1}, the pivot reciprocals and log sums."""
+    from paper_2503_17528_gb300 import _lib
+    v = ctypes.c_void_p
+    n, b, a = 5, 100, 3
+    nt, na = 4, 1
+    need = lib.bta_plan_entry_workspace_bytes(n, b, a)
+    parts = [n * b * b, (n - 1) * b * b, n * a * b, a * a, max(nt, na) * 32, n * nt + na]
+    assert need == sum(-(-8 * p // 256) * 256 for p in parts)
+    assert lib.bta_plan_entry_workspace_bytes(0, b, a) == 0
+    assert lib.bta_plan_entry_workspace_bytes(n, 0, a) == 0
+    ents = (_lib.BatchEntry * 1)()
+    e = ents[0]
+    e.n, e.b, e.a = n, b, a
+    e.diag, e.lower, e.arrow, e.tip = 4096, 4096, 4096, 4096
+    e.prec, e.ws, e.ws_bytes = 0, 4096, need
+    plan = v()
+    ok = _lib.PlanParams(0, 0, 0, 0)
+    assert lib.bta_plan_create(0, ctypes.addressof(ents), None, ctypes.byref(plan)) == -1
+    assert lib.bta_plan_create(1, None, None, ctypes.byref(plan)) == -2
+    assert lib.bta_plan_create(1, ctypes.addressof(ents), None, None) == -4
+    bad = _lib.PlanParams(0, 0, 3, 0)  # rows_per_item above 2
+    assert lib.bta_plan_create(1, ctypes.addressof(ents), ctypes.addressof(bad), ctypes.byref(plan)) == -3
+    for field, value in (("prec", 1), ("ws_bytes", need - 1), ("ws", 4097), ("tip", 0), ("b", 0)):
+        old = getattr(e, field)
+        setattr(e, field, value)
+        assert lib.bta_plan_create(1, ctypes.addressof(ents), ctypes.addressof(ok), ctypes.byref(plan)) == -2, field
+        setattr(e, field, old)
+    assert lib.bta_plan_run(None, None) == -1
+    assert lib.bta_plan_status(None, None, None, None) == -1
+    assert lib.bta_plan_describe(None, None, 0) == -1
+    assert lib.bta_plan_destroy(None) == 0
