@@ -467,7 +467,7 @@ def batch_measure(steps, warmup, dev, rank=0, world=1, oracle_sample=0, quick_tu
     return out
 
 
-PERSISTENT_QUICK = ((4, 32, 1), (3, 32, 1), (4, 128, 1), (4, 32, 2))
+PERSISTENT_QUICK = ((4, 8, 1), (4, 4, 1), (3, 8, 1), (4, 8, 2))
 
 
 def _batch_oracle_check(raw, W, logdets, sample):

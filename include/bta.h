@@ -208,19 +208,21 @@ int bta_factor_selinv_batched(int64_t count, const bta_batch_entry* entries, int
  * its Schur updates, the tip, the inverses L_ii^{-1}, the products G_i, H_i,
  * M_i, X_nn and the backward recurrence). On the device an operation becomes
  * ready when the operations it depends on have completed; the kernel's CTAs
- * take items of ready operations from two queues (small operations first), so
- * no CTA waits for a particular item.
+ * take items of ready operations from priority queues (operations of the
+ * matrices with the most remaining work first), so no CTA waits for a
+ * particular item.
  *
  * Tuning parameters (0 = automatic):
  *   ctas_per_sm    resident CTAs per SM (128 threads each; capped by occupancy)
- *   small_items    operations with at most this many items go to the priority
- *                  queue (0: 32)
+ *   levels         priority levels, 1..8 (0: 8): an operation's level is the
+ *                  share of its matrix's program still ahead of it, relative
+ *                  to the longest program; 1 serves operations in ready order
  *   rows_per_item  1 or 2 tile rows per update / product item (tile shape
  *                  32 x 32 or 64 x 32)
  */
 typedef struct bta_plan_params {
   int ctas_per_sm;
-  int small_items;
+  int levels;
   int rows_per_item;
   int reserved;
 } bta_plan_params;
@@ -263,8 +265,8 @@ int bta_plan_run(bta_plan plan, bta_stream_t stream);
 int bta_plan_status(bta_plan plan, int* timed_out, int64_t* info, bta_stream_t stream);
 
 /* bta_plan_describe -- out[0..nout-1] = grid CTAs, CTAs per SM, priority
- * threshold (items), rows per item, operations, items, algorithmic flops per
- * run, operations ready at the start. */
+ * levels, rows per item, operations, items, algorithmic flops per run,
+ * operations ready at the start. */
 int bta_plan_describe(bta_plan plan, int64_t* out, int nout);
 
 /* bta_plan_destroy -- frees the plan's device tables (synchronously; no run of

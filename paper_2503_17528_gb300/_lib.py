@@ -67,7 +67,7 @@ class BatchEntry(ctypes.Structure):
 
 
 class PlanParams(ctypes.Structure):
-    _fields_ = [("ctas_per_sm", ctypes.c_int), ("small_items", ctypes.c_int), ("rows_per_item", ctypes.c_int),
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("levels", ctypes.c_int), ("rows_per_item", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
 
 

@@ -90,12 +90,12 @@ class PersistentBatch:
     one device, overwritten in place with the selected inverse by run(). The plan
     (schedule and device tables) is built once here, for exactly these buffers;
     run() enqueues one launch on the current stream and can be captured in a
-    CUDA graph. Tuning parameters (0 = automatic): ctas_per_sm, small_items
-    (operations with at most this many tile items are served first),
-    rows_per_item (1 or 2).
+    CUDA graph. Tuning parameters (0 = automatic): ctas_per_sm, levels (priority
+    levels 1..8 of the device queues: operations of the matrices with the most
+    remaining work first; 1 = ready order), rows_per_item (1 or 2).
     """
 
-    def __init__(self, mats, ctas_per_sm=0, small_items=0, rows_per_item=0):
+    def __init__(self, mats, ctas_per_sm=0, levels=0, rows_per_item=0):
         self.mats = mats
         dev = mats[0][0].device
         self.device = dev
@@ -118,7 +118,7 @@ class PersistentBatch:
             e.prec = PREC_FP64
             e.ws = w.data_ptr() + (-w.data_ptr()) % 256
             e.ws_bytes = nbytes
-        self.params = _lib.PlanParams(int(ctas_per_sm), int(small_items), int(rows_per_item), 0)
+        self.params = _lib.PlanParams(int(ctas_per_sm), int(levels), int(rows_per_item), 0)
         self._plan = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.bta_plan_create(len(mats), ctypes.addressof(self.entries),
@@ -153,7 +153,7 @@ class PersistentBatch:
         lib = _lib.load()
         out = (ctypes.c_int64 * 8)()
         _check(lib.bta_plan_describe(self._plan, out, 8), "bta_plan_describe")
-        keys = ("grid", "ctas_per_sm", "small_items", "rows_per_item", "ops", "items", "flops", "ready_at_start")
+        keys = ("grid", "ctas_per_sm", "levels", "rows_per_item", "ops", "items", "flops", "ready_at_start")
         return dict(zip(keys, [int(x) for x in out]))
 
     def close(self):

@@ -23,23 +23,23 @@
 // An operation depends on at most four earlier operations of the same matrix.
 //
 // Scheduling is dynamic, on the device. An operation is ready once all the
-// operations it depends on have completed; ready operations wait in two FIFO
-// queues, a priority queue for small operations (at most `small_items` items:
-// the tile factorizations, panel solves and most of the recurrence, which gate
-// a matrix's progress) and a bulk queue. Every CTA repeatedly takes the next
-// item of the first ready operation that still has items (priority queue
-// first), runs it and counts it done; the CTA that completes an operation
-// counts one more finished dependency in each of its successors and appends
-// those that become ready to their queue. No CTA waits for a particular item:
-// a CTA that finds both queues empty polls until an operation completes, so
-// the kernel cannot deadlock, and it ends when every operation has completed.
-// The poll is bounded: after many polls with no operation completing anywhere
-// it sets the plan's error word and the CTAs return. At the start the first
-// operation of every matrix is ready, the largest matrices first. Data written
-// by one item and read by another is read through L2 (ld.global.cg): items of
-// the same tile can run on different SMs, whose L1 caches are not coherent.
-// The tuning parameters are the CTAs per SM, R (tile rows per item) and the
-// priority threshold.
+// operations it depends on have completed; ready operations wait in FIFO queues
+// by priority level: an operation's level is set by the number of operations
+// after it in its matrix's program relative to the longest program, so the
+// matrices with the most remaining work are served first (critical-path order).
+// Every CTA repeatedly takes the next item of the first ready operation that
+// still has items (highest level first), runs it and counts it done; the CTA
+// that completes an operation counts one more finished dependency in each of its
+// successors and appends those that become ready to their queue. No CTA waits
+// for a particular item: a CTA that finds every queue empty polls until an
+// operation completes, so the kernel cannot deadlock, and it ends when every
+// operation has completed. The poll is bounded: after many polls with no
+// operation completing anywhere it sets the plan's error word and the CTAs
+// return. At the start the first operation of every matrix is ready. Data
+// written by one item and read by another is read through L2 (ld.global.cg):
+// items of the same tile can run on different SMs, whose L1 caches are not
+// coherent. The tuning parameters are the CTAs per SM, R (tile rows per item)
+// and the number of priority levels (1: plain ready order).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -102,7 +102,7 @@ struct POp {
   int kind, nitems, arg, k;
   int ndeps;              // operations that must complete before this one is ready
   int succ_off, nsucc;    // the operations that depend on this one: succ[succ_off ..]
-  int prio;               // 0: priority queue (small operations), 1: bulk queue
+  int prio;               // queue 0..kQueues-1 (taken in that order)
 };
 
 struct PMat {
@@ -112,10 +112,12 @@ struct PMat {
 };
 
 // Counters of a run (zeroed, then seeded with the initially ready operations).
-// hdr: [0] error word, [1] completed operations, then per queue q (0: priority,
-// 1: bulk) [2 + 2q] head and [3 + 2q] reserved slots. A queue entry is op + 1
-// (0: reserved, not written yet); every operation enters a queue once, so each
-// queue has nops slots.
+// hdr: [0] error word, [1] completed operations, then per queue q [2 + 2q] head
+// and [3 + 2q] reserved slots. A queue entry is op + 1 (0: reserved, not written
+// yet); every operation enters a queue once, so each queue has nops slots.
+// Queue q holds the operations whose matrix has, after them, a remaining chain
+// of dependent operations in the q-th eighth of the longest one, longest first
+// (critical-path order); the queues are taken in that order.
 struct PDev {
   const POp* ops;
   const int* succ;
@@ -128,14 +130,15 @@ struct PDev {
   int* taken;      // [nops] items taken
   int* done;       // [nops] items completed
   int* sat;        // [nops] dependencies completed
-  int* queue;      // [2][nops]: queue q at queue + q * nops
+  int* queue;      // [kQueues][nops]: queue q at queue + q * nops
   unsigned long long* info;  // [matrices] first failed pivot row
   unsigned max_polls;
 };
 
 constexpr int kPThreads = 128;
 constexpr int kPMaxR = 2;
-constexpr int kCounterHeader = 64;  // ints of the run header (6 used)
+constexpr int kCounterHeader = 64;  // ints of the run header (2 + 2 kQueues used)
+constexpr int kQueues = 8;
 
 template <int MAXR>
 struct PSmem {
@@ -558,7 +561,18 @@ __device__ __forceinline__ int take_item(const PDev& d, int& item) {
   unsigned idle = 0;
   int seen = -1;
   for (;;) {
-    for (int q = 0; q < 2; ++q) {
+    // Heads and tails of all queues in one round of independent loads; then the
+    // first queue that is not empty.
+    int hd[kQueues], tl[kQueues];
+#pragma unroll
+    for (int q = 0; q < kQueues; ++q) {
+      hd[q] = __ldcv(d.hdr + 2 + 2 * q);
+      tl[q] = __ldcv(d.hdr + 3 + 2 * q);
+    }
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < kQueues; ++q) {
+      if (hd[q] >= tl[q]) continue;
       int* qh = d.hdr + 2 + 2 * q;
       for (;;) {
         const int h = ld_acquire(qh);
@@ -864,7 +878,7 @@ using namespace bta;
 struct bta_plan_s {
   int device = -1;
   int count = 0;
-  int grid = 0, small_items = 0, R = 1, ctas_per_sm = 0;
+  int grid = 0, levels = 0, R = 1, ctas_per_sm = 0;
   int nops = 0, ninit = 0;
   long long nitems = 0;
   double flops = 0.0;
@@ -872,8 +886,8 @@ struct bta_plan_s {
   void* counters = nullptr;  // header, taken, done, sat, two queues, info
   size_t counter_bytes = 0;
   const int* seed_hdr = nullptr;    // device: header values of a fresh run
-  const int* seed_queue[2] = {nullptr, nullptr};  // device: initially ready operations
-  int seed_len[2] = {0, 0};
+  const int* seed_queue[kQueues] = {};  // device: initially ready operations
+  int seed_len[kQueues] = {};
   const void* kernel = nullptr;
   PDev d{};
 };
@@ -893,7 +907,7 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   *out = nullptr;
   bta_plan_params prm{};
   if (params) prm = *params;
-  if (prm.ctas_per_sm < 0 || prm.ctas_per_sm > 16 || prm.small_items < 0 ||
+  if (prm.ctas_per_sm < 0 || prm.ctas_per_sm > 16 || prm.levels < 0 || prm.levels > kQueues ||
       prm.rows_per_item < 0 || prm.rows_per_item > kPMaxR)
     return -3;
   for (int64_t k = 0; k < count; ++k) {
@@ -907,7 +921,7 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
     if (e.logdet_out && ((uintptr_t)e.logdet_out % 8)) return -2;
   }
   const int R = prm.rows_per_item ? prm.rows_per_item : 1;
-  const int small = prm.small_items ? prm.small_items : 32;
+  const int levels = prm.levels ? prm.levels : kQueues;
   const PKernel kern = pick_kernel(R);
   int per_sm = 0, sms = 0;
   cudaError_t ce = plan_occupancy(kern, &per_sm, &sms);
@@ -932,15 +946,25 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   std::vector<int64_t> order(count);
   for (int64_t k = 0; k < count; ++k) order[k] = k;
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return fl[x] > fl[y]; });
+  // Critical-path priority: an operation's queue is set by the number of
+  // operations after it in its matrix's program (a chain, apart from the
+  // prologue's independent products), relative to the longest program. Matrices
+  // with the most remaining work are served first; otherwise their chains, slowed
+  // by the other matrices' items, end the run alone.
   Builder bld;
   bld.R = R;
   std::vector<POp> ops;
   std::vector<std::vector<int>> succ;
-  std::vector<int> init[2];
+  std::vector<int> init[kQueues];
   long long nitems = 0;
+  std::vector<std::vector<HOp>> progs(count);
+  size_t longest = 1;
   for (int64_t m : order) {
-    std::vector<HOp> prog;
-    bld.add_matrix((int)m, entries[m], prog);
+    bld.add_matrix((int)m, entries[m], progs[m]);
+    longest = std::max(longest, progs[m].size());
+  }
+  for (int64_t m : order) {
+    const std::vector<HOp>& prog = progs[m];
     const int base = (int)ops.size();
     if ((size_t)base + prog.size() > (size_t)0x3fffffff) return -1;
     succ.resize(base + prog.size());
@@ -956,7 +980,8 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
         if (!dup) deps[nd++] = dl;
       }
       o.ndeps = nd;
-      o.prio = o.nitems <= small ? 0 : 1;
+      const double rem = (double)(prog.size() - h.local) / (double)longest;  // in (0, 1]
+      o.prio = std::min(levels - 1, std::max(0, (int)((1.0 - rem) * levels)));
       const int gi = base + h.local;
       for (int q = 0; q < nd; ++q) succ[base + deps[q]].push_back(gi);
       if (nd == 0) init[o.prio].push_back(gi);
@@ -974,23 +999,24 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   // Seed image of a run: header (queue tails = initially ready counts) and the
   // initial queue entries (op + 1).
   std::vector<int> seed_hdr(kCounterHeader, 0);
-  seed_hdr[3] = (int)init[0].size();
-  seed_hdr[5] = (int)init[1].size();
-  std::vector<int> seed_q[2];
-  for (int q = 0; q < 2; ++q)
+  std::vector<int> seed_q[kQueues];
+  for (int q = 0; q < kQueues; ++q) {
+    seed_hdr[3 + 2 * q] = (int)init[q].size();
     for (int v : init[q]) seed_q[q].push_back(v + 1);
+  }
 
   bta_plan_s* P = new (std::nothrow) bta_plan_s;
   if (!P) return (int)cudaErrorMemoryAllocation;
   cudaGetDevice(&P->device);
   P->count = (int)count;
   P->grid = G;
-  P->small_items = small;
+  P->levels = levels;
   P->R = R;
   P->kernel = (const void*)kern;
   P->ctas_per_sm = occ;
   P->nops = nops;
-  P->ninit = (int)(init[0].size() + init[1].size());
+  P->ninit = 0;
+  for (int q = 0; q < kQueues; ++q) P->ninit += (int)init[q].size();
   P->nitems = nitems;
   P->flops = flops;
   struct Part {
@@ -1005,7 +1031,13 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
                         {bld.mats.data(), bld.mats.size() * sizeof(PMat)},
                         {seed_hdr.data(), seed_hdr.size() * sizeof(int)},
                         {seed_q[0].data(), seed_q[0].size() * sizeof(int)},
-                        {seed_q[1].data(), seed_q[1].size() * sizeof(int)}};
+                        {seed_q[1].data(), seed_q[1].size() * sizeof(int)},
+                        {seed_q[2].data(), seed_q[2].size() * sizeof(int)},
+                        {seed_q[3].data(), seed_q[3].size() * sizeof(int)},
+                        {seed_q[4].data(), seed_q[4].size() * sizeof(int)},
+                        {seed_q[5].data(), seed_q[5].size() * sizeof(int)},
+                        {seed_q[6].data(), seed_q[6].size() * sizeof(int)},
+                        {seed_q[7].data(), seed_q[7].size() * sizeof(int)}};
   constexpr int kParts = sizeof(parts) / sizeof(parts[0]);
   size_t total = 0, at[kParts];
   for (int q = 0; q < kParts; ++q) {
@@ -1013,7 +1045,7 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
     total += align256(parts[q].bytes + 1);
   }
   const size_t n_int = (size_t)nops;
-  P->counter_bytes = align256((kCounterHeader + 5 * n_int) * sizeof(int)) +
+  P->counter_bytes = align256((kCounterHeader + (3 + kQueues) * n_int) * sizeof(int)) +
                      align256(count * sizeof(unsigned long long));
   ce = cudaMalloc(&P->desc, total);
   if (ce == cudaSuccess) ce = cudaMalloc(&P->counters, P->counter_bytes);
@@ -1037,10 +1069,10 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   P->d.trtris = (const PTrtri*)(D + at[4]);
   P->d.mats = (const PMat*)(D + at[5]);
   P->seed_hdr = (const int*)(D + at[6]);
-  P->seed_queue[0] = (const int*)(D + at[7]);
-  P->seed_queue[1] = (const int*)(D + at[8]);
-  P->seed_len[0] = (int)seed_q[0].size();
-  P->seed_len[1] = (int)seed_q[1].size();
+  for (int q = 0; q < kQueues; ++q) {
+    P->seed_queue[q] = (const int*)(D + at[7 + q]);
+    P->seed_len[q] = (int)seed_q[q].size();
+  }
   int* c = (int*)P->counters;
   P->d.nops = nops;
   P->d.hdr = c;
@@ -1049,7 +1081,7 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   P->d.sat = P->d.done + n_int;
   P->d.queue = P->d.sat + n_int;
   P->d.info = (unsigned long long*)((char*)P->counters +
-                                    align256((kCounterHeader + 5 * n_int) * sizeof(int)));
+                                    align256((kCounterHeader + (3 + kQueues) * n_int) * sizeof(int)));
   P->d.max_polls = 1u << 22;  // polls (128 ns sleeps) without any operation completing
   *out = P;
   return 0;
@@ -1068,7 +1100,7 @@ int bta_plan_run(bta_plan plan, bta_stream_t stream) {
   e = cudaMemsetAsync(P->counters, 0, P->counter_bytes, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(P->d.hdr, P->seed_hdr, kCounterHeader * sizeof(int), cudaMemcpyDeviceToDevice, s);
-  for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+  for (int q = 0; q < kQueues && e == cudaSuccess; ++q)
     if (P->seed_len[q])
       e = cudaMemcpyAsync(P->d.queue + q * n_ops(P), P->seed_queue[q], P->seed_len[q] * sizeof(int),
                           cudaMemcpyDeviceToDevice, s);
@@ -1110,7 +1142,7 @@ int bta_plan_describe(bta_plan plan, int64_t* out, int nout) {
   bta_plan_s* P = plan;
   if (!P) return -1;
   if (!out || nout < 1) return -2;
-  const int64_t v[8] = {P->grid, P->ctas_per_sm, P->small_items, P->R, P->nops, P->nitems,
+  const int64_t v[8] = {P->grid, P->ctas_per_sm, P->levels, P->R, P->nops, P->nitems,
                         (int64_t)P->flops, P->ninit};
   for (int q = 0; q < nout && q < 8; ++q) out[q] = v[q];
   return 0;

@@ -85,14 +85,14 @@ def tune(mats, pristine, policies=None, streams=STREAMS, reps=2, save=True):
     return res
 
 
-# Candidates of the persistent kernel: (CTAs per SM, priority threshold in items,
-# tile rows per item). Both builds of the kernel hold at most 4 CTAs per SM.
+# Candidates of the persistent kernel: (CTAs per SM, priority levels, tile rows
+# per item). Both builds of the kernel hold at most 4 CTAs per SM.
 PERSISTENT_CANDIDATES = tuple((c, w, r) for r in (1, 2) for c in ((2, 3, 4) if r == 1 else (2, 4))
-                              for w in (8, 32, 128))
+                              for w in (1, 4, 8))
 
 
 def tune_persistent(mats, pristine, candidates=None, reps=2, save=True):
-    """Times each (ctas_per_sm, small_items, rows_per_item) candidate of the persistent
+    """Times each (ctas_per_sm, levels, rows_per_item) candidate of the persistent
     batched kernel on the actual batch (graph replays) and caches the fastest
     under the key 'persistent|' + signature. Returns {"params", "ms", "table"}."""
     from .batched import PersistentBatch
@@ -104,8 +104,8 @@ def tune_persistent(mats, pristine, candidates=None, reps=2, save=True):
                 if x is not None and x.numel():
                     x.copy_(y)
 
-    for cps, small, rows in (candidates or PERSISTENT_CANDIDATES):
-        pb = PersistentBatch(mats, ctas_per_sm=cps, small_items=small, rows_per_item=rows)
+    for cps, levels, rows in (candidates or PERSISTENT_CANDIDATES):
+        pb = PersistentBatch(mats, ctas_per_sm=cps, levels=levels, rows_per_item=rows)
         restore()
         pb.run()
         torch.cuda.synchronize()
@@ -127,10 +127,10 @@ def tune_persistent(mats, pristine, candidates=None, reps=2, save=True):
         desc = pb.describe()
         del graph
         pb.close()
-        table.append({"ctas_per_sm": desc["ctas_per_sm"], "small_items": desc["small_items"],
+        table.append({"ctas_per_sm": desc["ctas_per_sm"], "levels": desc["levels"],
                       "rows_per_item": rows, "ms": min(times)})
     best = min(table, key=lambda r: r["ms"])
-    res = {"params": {"ctas_per_sm": best["ctas_per_sm"], "small_items": best["small_items"],
+    res = {"params": {"ctas_per_sm": best["ctas_per_sm"], "levels": best["levels"],
                       "rows_per_item": best["rows_per_item"]}, "ms": best["ms"], "table": table}
     if save:
         cache = _load()

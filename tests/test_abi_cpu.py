@@ -126,8 +126,8 @@ def test_persistent_plan_checks_arguments_before_the_gpu(lib):
     assert lib.bta_plan_create(0, ctypes.addressof(ents), None, ctypes.byref(plan)) == -1
     assert lib.bta_plan_create(1, None, None, ctypes.byref(plan)) == -2
     assert lib.bta_plan_create(1, ctypes.addressof(ents), None, None) == -4
-    bad = _lib.PlanParams(0, 0, 3, 0)  # rows_per_item above 2
-    assert lib.bta_plan_create(1, ctypes.addressof(ents), ctypes.addressof(bad), ctypes.byref(plan)) == -3
+    for bad in (_lib.PlanParams(0, 0, 3, 0), _lib.PlanParams(0, 9, 0, 0), _lib.PlanParams(-1, 0, 0, 0)):
+        assert lib.bta_plan_create(1, ctypes.addressof(ents), ctypes.addressof(bad), ctypes.byref(plan)) == -3
     for field, value in (("prec", 1), ("ws_bytes", need - 1), ("ws", 4097), ("tip", 0), ("b", 0)):
         old = getattr(e, field)
         setattr(e, field, value)

@@ -51,9 +51,9 @@ def test_persistent_matches_oracle():
     assert desc["grid"] >= desc["ctas_per_sm"] >= 1 and desc["ops"] > 0 and desc["items"] >= desc["ops"]
 
 
-@pytest.mark.parametrize("params", [dict(rows_per_item=2), dict(small_items=1),
-                                    dict(small_items=10000, ctas_per_sm=2),
-                                    dict(ctas_per_sm=1, small_items=3, rows_per_item=2)])
+@pytest.mark.parametrize("params", [dict(rows_per_item=2), dict(levels=1),
+                                    dict(levels=3, ctas_per_sm=2),
+                                    dict(ctas_per_sm=1, levels=8, rows_per_item=2)])
 def test_parameters_change_schedule_not_results(params):
     raw, mats = _make()
     base = PersistentBatch(mats)
