@@ -240,9 +240,11 @@ size_t bta_plan_entry_workspace_bytes(int64_t n, int64_t b, int64_t a);
  * device tables (cudaMalloc, on the current device, which must hold the
  * buffers). Entries: prec must be BTA_PREC_FP64; ws of at least
  * bta_plan_entry_workspace_bytes(n, b, a) bytes, 256-byte aligned; logdet_out
- * may be NULL. params may be NULL (all automatic). Synchronous. Returns 0 and
- * *out, -1 for count out of [1, 65536], -2 for an invalid entry, -3 for invalid
- * params, -4 for a NULL out, > 0 for a CUDA error.
+ * may be NULL. Size limits per entry: b, a <= 32768, n <= 2^20 and
+ * n (ceil(b/32))^2 <= 1.5e9 (the tiles of one product over all blocks). params
+ * may be NULL (all automatic). Synchronous. Returns 0 and *out, -1 for count out
+ * of [1, 65536], -2 for an invalid entry, -3 for invalid params, -4 for a NULL
+ * out, > 0 for a CUDA error.
  */
 int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_plan_params* params,
                     bta_plan* out);

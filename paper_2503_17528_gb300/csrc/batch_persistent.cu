@@ -913,7 +913,10 @@ int bta_plan_create(int64_t count, const bta_batch_entry* entries, const bta_pla
   for (int64_t k = 0; k < count; ++k) {
     const bta_batch_entry& e = entries[k];
     if (e.n < 1 || e.b < 1 || e.a < 0 || e.b > 32768 || e.a > 32768) return -2;
-    if (e.n > (1 << 20) || (double)e.n * ((e.b + T - 1) / T) > 1e8) return -2;
+    // Item indices are ints: the largest operation (a product over all blocks,
+    // n (b/32)^2 tiles) must stay well below 2^31.
+    const double nt = (double)((e.b + T - 1) / T);
+    if (e.n > (1 << 20) || (double)e.n * nt * nt > 1.5e9) return -2;
     if (!e.diag || (e.n > 1 && !e.lower) || (e.a > 0 && (!e.arrow || !e.tip))) return -2;
     if (e.prec != BTA_PREC_FP64) return -2;
     if (!e.ws || ((uintptr_t)e.ws % 256) || e.ws_bytes < entry_ws(e.n, e.b, e.a, nullptr, nullptr))

@@ -137,3 +137,15 @@ def test_persistent_plan_checks_arguments_before_the_gpu(lib):
     assert lib.bta_plan_status(None, None, None, None) == -1
     assert lib.bta_plan_describe(None, None, 0) == -1
     assert lib.bta_plan_destroy(None) == 0
+
+
+def test_persistent_plan_rejects_item_counts_past_int_range(lib):
+    """One product over all blocks has n (b/32)^2 tile items, indexed by ints."""
+    from paper_2503_17528_gb300 import _lib
+    ents = (_lib.BatchEntry * 1)()
+    e = ents[0]
+    e.n, e.b, e.a = 1 << 20, 2048, 0
+    e.diag, e.lower = 4096, 4096
+    e.prec, e.ws, e.ws_bytes = 0, 4096, 1 << 62
+    plan = ctypes.c_void_p()
+    assert lib.bta_plan_create(1, ctypes.addressof(ents), None, ctypes.byref(plan)) == -2
